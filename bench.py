@@ -1,0 +1,300 @@
+#!/usr/bin/env python3
+"""Throughput of the RSST finite-volume step on GB300.
+
+Metric: cell-updates per second per RK stage (cells x 2 stages per step /
+time).  Default workload: the 2D periodic 512 x 512 float64 shear layer at
+Mach 0.01 (density ratio 10, tanh width 0.02, xi = 30, semi-conservative
+PVS form), adaptive CFL dt.  One step = one SSP-RK2 step = two fused stage
+kernels.  The state (8 MB per field set) fits in L2, so a 256 MiB buffer is
+written between timed steps (outside the timed events) to flush it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line (rank 0).  --impl reference times the CPU oracle (test
+infrastructure, run here only as the reference arm) on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+import torch  # noqa: E402
+
+METRIC = "cell-updates/s per RK stage"
+UNIT = "cell-updates/s"
+L2_FLUSH_BYTES = 256 << 20
+
+# float64 operations per cell per stage of the fused kernel, counted from the
+# algorithm: 2D, per face 122 (+2 div, 4 sqrt),
+# divergence 8, correction + force + RK ~40 (+3 div, 2 sqrt); div and sqrt
+# counted as one operation each.
+FP64_FLOPS_PER_CELL_STAGE_2D = 2 * (122 + 6) + 8 + 45
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def fp64_peak_tflops(sm_mhz: float) -> float:
+    """GB300 float64 rate from unit counts and clock: 152 SMs x 1 DFMA per SM
+    per clock (2 flops) x clock; the unit count is the one the FP64 probe
+    measured."""
+    return 152 * 1.0 * 2.0 * sm_mhz * 1e6 / 1e12
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons every 200 ms during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=2)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    return world, rank, local
+
+
+def _barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def _max_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def workload(args):
+    from paper_1812_04135_gb300 import inputs
+    return inputs.shear_layer_2d(args.n, args.n, xi=30.0, variant=args.variant, ratio=10.0)
+
+
+def cpu_baseline(w, seconds: float):
+    """The oracle as it stands on the host cores: full-grid steps until ~``seconds``."""
+    from oracle import rsst_oracle as ro
+    from oracle.workload import problem_from
+    prob, U = problem_from(w)
+    cells = int(np.prod(w["n"]))
+    t0 = time.perf_counter()
+    steps = 0
+    while True:
+        dt = ro.cfl_dt(U, prob)
+        U = ro.ssp_rk2_step(U, dt, prob)
+        steps += 1
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            break
+    return {"value": cells * 2 * steps / el, "unit": UNIT, "cores": torch.get_num_threads(), "kind": "oracle",
+            "sample": f"{steps} full-grid SSP-RK2 steps of the {w['n'][0]}x{w['n'][1]} workload "
+                      f"({el:.1f} s, torch CPU float64)"}
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    w = workload(args)
+    from oracle import rsst_oracle as ro
+    from oracle.workload import problem_from
+    prob, U = problem_from(w)
+    cells = int(np.prod(w["n"]))
+    for _ in range(args.warmup):
+        U = ro.ssp_rk2_step(U, ro.cfl_dt(U, prob), prob)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        U = ro.ssp_rk2_step(U, ro.cfl_dt(U, prob), prob)
+    el = time.perf_counter() - t0
+    v = cells * 2 * args.steps / el
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": _config(args, w),
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": torch.get_num_threads(), "kind": "oracle",
+                             "sample": f"{args.steps} timed full-grid steps after {args.warmup} warm-up steps"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def _config(args, w):
+    return {"workload": f"2D periodic shear layer {w['n'][0]}x{w['n'][1]} FP64, Mach 0.01, density ratio 10, "
+                        f"xi=30, {args.variant.upper()} form, adaptive CFL 0.4",
+            "cells": int(np.prod(w["n"])), "variant": args.variant, "precision": "fp64",
+            "l2": "256 MiB buffer written between timed steps (state fits in L2)",
+            "parallelism": f"replicas x{args.gpus}"}
+
+
+def run_gpu(args, world, rank, local):
+    from paper_1812_04135_gb300 import rsst
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w = workload(args)
+    cells = int(np.prod(w["n"]))
+    stream = torch.cuda.current_stream(dev)
+    s = rsst.Solver(w, "fp64", stream=stream)
+    U0 = torch.from_numpy(w["U"]).to(dev)
+    s.set_state(U0)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    for _ in range(args.warmup):
+        s.step(1)
+    s.sync()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    l0 = s.launches()
+    _barrier(world)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        w0 = time.perf_counter()
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            ev[k][0].record(stream)
+            s.step(1)
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - w0
+    _barrier(world)
+    launches = s.launches() - l0
+    s.sync()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    t_dev = sum(step_ms) / 1e3
+    t_max = _max_over_ranks(t_dev, world)
+    value = cells * 2 * args.steps * world / t_max
+
+    # end to end through the C ABI with host buffers: H2D state, step, D2H state
+    host_in = torch.from_numpy(w["U"]).pin_memory()
+    host_out = torch.empty_like(host_in).pin_memory()
+    rsst.rsst_set_state(s.h, host_in, on_host=True)
+    s.step(1)
+    s.sync()
+    _barrier(world)
+    torch.cuda.synchronize()
+    e0 = time.perf_counter()
+    for _ in range(args.steps):
+        rsst.rsst_set_state(s.h, host_in, on_host=True)
+        s.step(1)
+        rsst.rsst_get_state(s.h, host_out, on_host=True)
+    torch.cuda.synchronize()
+    e_el = _max_over_ranks(time.perf_counter() - e0, world)
+    e2e = cells * 2 * args.steps * world / e_el
+    nbytes = host_in.numel() * 8
+    s.close()
+
+    if rank != 0:
+        return
+    peaks, src = _peaks()
+    c = clk.summary()
+    sm_mhz = c["sm_mhz"] or peaks.get("clocks_under_load", {}).get("sm_mhz_median", 1900.0)
+    launch_s = t_dev / (2 * args.steps)
+    flops = FP64_FLOPS_PER_CELL_STAGE_2D * cells
+    peak_tf = fp64_peak_tflops(sm_mhz)
+    achieved_tf = flops / launch_s / 1e12
+    alg_bytes = 40 * cells * 2          # 2.5 * nvar * 8 B per cell-stage, nvar = 4
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_max / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": _config(args, w),
+            "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": peak_tf, "unit": "TFLOP/s",
+                         "frac": achieved_tf / peak_tf, "traffic": None,
+                         "peak_source": f"float64: 152 SMs x 2 flop/clk x {sm_mhz:.0f} MHz (unit count measured)",
+                         "hbm_achieved_gbs": alg_bytes / launch_s / 1e9, "hbm_peak_gbs": peaks["hbm_gbs"],
+                         "hbm_frac": alg_bytes / launch_s / 1e9 / peaks["hbm_gbs"], "hbm_peak_source": src},
+            "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
+            "gpu_launches": launches, "clocks": c, "wall_s": wall,
+            "step_ms_min": min(step_ms), "step_ms_median": statistics.median(step_ms)}
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(w, args.cpu_seconds)
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--n", type=int, default=512)
+    ap.add_argument("--variant", default="pvs")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world, rank, local = _dist()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_gpu(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

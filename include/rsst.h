@@ -1,0 +1,148 @@
+/*
+ * librsst — GB300 (sm_103a) explicit finite-volume step of the reduced speed
+ * of sound technique (RSST) for the Euler equations.
+ *
+ * Method: Iijima, Hotta & Imada, "Semi-conservative reduced speed of sound
+ * technique for low Mach number flows with large density variations"
+ * (arXiv:1812.04135).  One call of rsst_step advances the conserved state
+ * U = (rho, m, E) by SSP-RK2 steps of the scheme of Sec. 4.2 (MUSCL with the
+ * monotonized-central limiter, local Lax-Friedrichs flux with
+ * c_tot = |V| + a/xi, CFL number 0.4), with the time derivative reduced by
+ * one of the semi-conservative forms (Sec. 3.2 PVS; App. A DVS, PMS, DMS,
+ * PD) and the external force of App. B.
+ *
+ * Conventions for every entry point:
+ *  - Return value: RSST_OK (0) or a negative RSST_E* code; nothing aborts,
+ *    prints or exits.  rsst_last_error() gives a message for the calling
+ *    thread's last failure.
+ *  - State layout seen by the caller (device or host memory, float64):
+ *    structure of arrays [nvar][nz][ny][nx], x fastest, nvar = 2 + ndim,
+ *    components (rho, m_x[, m_y[, m_z]], E).  Unused dimensions have size 1.
+ *  - The caller owns every buffer it passes.  The library owns its working
+ *    state (padded, with two ghost layers per active axis), its CFL scalars,
+ *    flags, graphs and checkpoints; rsst_destroy frees them.
+ *  - All GPU work is issued on the stream given to rsst_init (a
+ *    cudaStream_t, NULL for the legacy default stream).  Calls documented
+ *    as asynchronous return once the work is queued.
+ *  - A non-physical state (rho <= 0, P <= 0 or a non-finite value) found
+ *    by a step sets a sticky device flag; the next synchronous call returns
+ *    RSST_ENONPHYSICAL.  The output is still written.  No floors are applied.
+ */
+#ifndef RSST_H
+#define RSST_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RSST_OK            0
+#define RSST_EINVAL       -1  /* bad argument or configuration */
+#define RSST_ECUDA        -2  /* a CUDA runtime/driver call failed */
+#define RSST_ENONPHYSICAL -3  /* rho <= 0, P <= 0 or NaN/Inf produced */
+#define RSST_ETIMEOUT     -4  /* a bounded device wait gave up */
+#define RSST_EUNSUPPORTED -5  /* valid request this build does not provide */
+#define RSST_ENOMEM       -6  /* device allocation failed */
+
+/* Forms of the reduced time derivative (Sec. 3.2 and App. A). */
+typedef enum {
+  RSST_EULER = 0, /* no reduction: conservative Euler */
+  RSST_DVS = 1,   /* "original" RSST, density reduced, App. A.1 */
+  RSST_PVS = 2,   /* "semi-conservative", pressure reduced, Sec. 3.2 */
+  RSST_DMS = 3,   /* momentum conserving, density reduced, App. A.3 */
+  RSST_PMS = 4,   /* momentum conserving, pressure reduced, App. A.2 */
+  RSST_PD = 5     /* mass and momentum conserving, App. A.4 */
+} rsst_variant;
+
+typedef enum {
+  RSST_FP64 = 0,      /* state stored and computed in float64 */
+  RSST_FP32_PERT = 1  /* float32 perturbation about a float64 background */
+} rsst_precision;
+
+typedef enum { RSST_BC_PERIODIC = 0, RSST_BC_REFLECT = 1 } rsst_bc;
+
+/* Run configuration.  Arrays are ordered (x, y, z); entries beyond ndim are
+ * ignored.  The background (bg_rho, bg_p; HOST pointers, copied by
+ * rsst_init) is a hydrostatic profile along axis `vertical` with
+ * n[vertical] + 4 values: index k holds cell k - 2 (two ghost cells at each
+ * end).  It sets the reflecting-wall ghost cells along `vertical`
+ * (ghost = U0(ghost) + mirror(U - U0)(image), U0 = (rho0, 0, P0/(gamma-1)))
+ * and, in RSST_FP32_PERT mode, the float64 state the float32 perturbation is
+ * stored about.  With vertical = -1 there is no background (in
+ * RSST_FP32_PERT mode the float32 state is then the full state).  On a
+ * periodic vertical axis the ghost entries are ignored (taken by wrap). */
+typedef struct rsst_config {
+  int32_t ndim;        /* 1, 2 or 3 */
+  int32_t n[3];        /* interior cells per axis, >= 2 on active axes */
+  double dx[3];        /* cell widths */
+  int32_t bc[3];       /* rsst_bc per axis, both ends */
+  int32_t variant;     /* rsst_variant */
+  int32_t precision;   /* rsst_precision */
+  double xi;           /* reduction rate, >= 1 (constant, Sec. 4.3) */
+  double gamma;        /* ratio of specific heats (ideal gas) */
+  double cfl;          /* Courant number (0.4 in Sec. 4.2) */
+  double grav[3];      /* constant acceleration F of App. B */
+  int32_t vertical;    /* background axis, or -1 */
+  int32_t reserved;
+  const double* bg_rho;
+  const double* bg_p;
+} rsst_config;
+
+typedef struct rsst_handle rsst_handle;
+
+/* Create a solver for one run.  Allocates the working state on the current
+ * CUDA device.  `stream` is a cudaStream_t (may be NULL).  Synchronous. */
+int rsst_init(rsst_handle** h, const rsst_config* cfg, void* stream);
+
+/* Free everything the handle owns.  Safe on NULL. */
+void rsst_destroy(rsst_handle* h);
+
+/* Load the full float64 state (caller layout above) from device memory
+ * (on_host = 0) or host memory (on_host = 1), fill the ghost cells, clear
+ * the non-physical flag and compute the CFL maximum of the new state.
+ * Asynchronous for device input; host input is copied with cudaMemcpyAsync
+ * (pinned memory keeps it asynchronous). */
+int rsst_set_state(rsst_handle* h, const double* U, int on_host);
+
+/* Write the full float64 state (background added back in RSST_FP32_PERT
+ * mode) to device (on_host = 0) or host (on_host = 1) memory.  Synchronous
+ * for host output; returns RSST_ENONPHYSICAL if the flag is set. */
+int rsst_get_state(rsst_handle* h, double* U, int on_host);
+
+/* Advance nsteps SSP-RK2 steps (Sec. 4.2).  dt > 0: fixed step.  dt <= 0:
+ * each step takes dt = cfl / max_cells sum_d c_tot/dx_d from the state at
+ * its start, entirely on the device.  Each step is two fused stage kernels
+ * (reconstruction, LLF flux, divergence, RSST correction, force, RK update,
+ * ghost cells; the second also reduces the CFL maximum).  Asynchronous. */
+int rsst_step(rsst_handle* h, double dt, int nsteps);
+
+/* The step the next adaptive rsst_step will take (cfl / CFL maximum of the
+ * current state).  Synchronous. */
+int rsst_dt(rsst_handle* h, double* dt_out);
+
+/* Wait for queued work; RSST_ENONPHYSICAL if a step flagged the state. */
+int rsst_sync(rsst_handle* h);
+
+/* Sum over cells of each conserved variable times the cell volume, in
+ * float64, deterministic order (fixed-shape two-level tree).  In
+ * RSST_FP32_PERT mode the background's sum (float64) is added to the sum
+ * of the perturbation.  `sums` is host memory with nvar entries.
+ * Synchronous. */
+int rsst_conserved_sums(rsst_handle* h, double* sums);
+
+/* Number of kernels the library launched through this handle so far. */
+int64_t rsst_kernel_launches(const rsst_handle* h);
+
+/* sizeof(rsst_config) as compiled into the library (binding check). */
+size_t rsst_config_size(void);
+
+/* Message describing the calling thread's most recent failure. */
+const char* rsst_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RSST_H */

@@ -1,0 +1,298 @@
+// C ABI of librsst (declared in include/rsst.h): handle management, state
+// transfer, step orchestration on the caller's stream, diagnostics.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+
+#include "rsst_internal.h"
+
+static thread_local char g_err[512] = "";
+
+void rsst_set_error(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof g_err, fmt, ap);
+  va_end(ap);
+}
+
+extern "C" const char* rsst_last_error(void) { return g_err; }
+
+#define CUDA_TRY(call)                                                              \
+  do {                                                                              \
+    const cudaError_t e_ = (call);                                                  \
+    if (e_ != cudaSuccess) {                                                        \
+      rsst_set_error("%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+      return RSST_ECUDA;                                                            \
+    }                                                                               \
+  } while (0)
+
+#define RC_TRY(call)          \
+  do {                        \
+    const int rc_ = (call);   \
+    if (rc_ != RSST_OK) return rc_; \
+  } while (0)
+
+struct rsst_handle {
+  rsst_config cfg;
+  Geom g;
+  Phys p;
+  cudaStream_t stream;
+  size_t elem;          // bytes per stored scalar
+  void* buf[2];         // padded state: buf[0] = U^n, buf[1] = U*
+  double* d_bg;         // [2][bg_len] rho0, E0 (float64), or null
+  int bg_len;
+  double* d_scal;       // [0..1] CFL slots, [2] dt, [8..15] sums
+  unsigned int* d_flag;
+  double* d_partial;    // sums partials
+  double* d_stage;      // caller-layout staging for host transfers
+  double* h_small;      // pinned host scratch for small read-backs
+  int slot;
+  int64_t launches;
+};
+
+static int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+
+static int validate(const rsst_config* c) {
+  if (!c) { rsst_set_error("config is NULL"); return RSST_EINVAL; }
+  if (c->ndim < 1 || c->ndim > 3) { rsst_set_error("ndim must be 1, 2 or 3 (got %d)", c->ndim); return RSST_EINVAL; }
+  for (int d = 0; d < c->ndim; ++d) {
+    if (c->n[d] < 2) { rsst_set_error("n[%d] must be >= 2 (got %d)", d, c->n[d]); return RSST_EINVAL; }
+    if (!(c->dx[d] > 0.0) || !std::isfinite(c->dx[d])) { rsst_set_error("dx[%d] must be > 0", d); return RSST_EINVAL; }
+    if (c->bc[d] != RSST_BC_PERIODIC && c->bc[d] != RSST_BC_REFLECT) { rsst_set_error("bc[%d] invalid", d); return RSST_EINVAL; }
+  }
+  if (c->variant < RSST_EULER || c->variant > RSST_PD) { rsst_set_error("variant %d invalid", c->variant); return RSST_EINVAL; }
+  if (c->precision != RSST_FP64 && c->precision != RSST_FP32_PERT) { rsst_set_error("precision %d invalid", c->precision); return RSST_EINVAL; }
+  if (!(c->xi >= 1.0) || !std::isfinite(c->xi)) { rsst_set_error("xi must be finite and >= 1 (got %g)", c->xi); return RSST_EINVAL; }
+  if (!(c->gamma > 1.0)) { rsst_set_error("gamma must be > 1"); return RSST_EINVAL; }
+  if (!(c->cfl > 0.0)) { rsst_set_error("cfl must be > 0"); return RSST_EINVAL; }
+  if (c->vertical < -1 || c->vertical >= c->ndim) { rsst_set_error("vertical axis %d invalid", c->vertical); return RSST_EINVAL; }
+  if (c->vertical >= 0 && (!c->bg_rho || !c->bg_p)) { rsst_set_error("background profiles required when vertical >= 0"); return RSST_EINVAL; }
+  int64_t cells = 1;
+  for (int d = 0; d < c->ndim; ++d) cells *= c->n[d];
+  if (cells > (int64_t)1 << 31) { rsst_set_error("grid too large (%lld cells)", (long long)cells); return RSST_EINVAL; }
+  return RSST_OK;
+}
+
+static void make_geom(const rsst_config* c, size_t elem, Geom* g) {
+  memset(g, 0, sizeof *g);
+  g->ndim = c->ndim;
+  for (int d = 0; d < 3; ++d) g->n[d] = d < c->ndim ? c->n[d] : 1;
+  g->gy = c->ndim >= 2 ? RSST_G : 0;
+  g->gz = c->ndim >= 3 ? RSST_G : 0;
+  g->xoff = (int)(32 / elem);
+  g->py = c->ndim >= 2 ? g->n[1] + 2 * RSST_G : 1;
+  g->pz = c->ndim >= 3 ? g->n[2] + 2 * RSST_G : 1;
+  g->pitch = round_up(g->xoff + g->n[0] + RSST_G, 32);
+  g->plane = g->pitch * g->py;
+  g->fstride = round_up(g->plane * g->pz, 32);
+  g->ncells = (int64_t)g->n[0] * g->n[1] * g->n[2];
+}
+
+static void make_phys(const rsst_config* c, Phys* p) {
+  memset(p, 0, sizeof *p);
+  p->gamma = c->gamma;
+  p->gm1 = c->gamma - 1.0;
+  p->inv_gm1 = 1.0 / (c->gamma - 1.0);
+  p->xi = c->xi;
+  p->inv_xi = 1.0 / c->xi;
+  p->f = 1.0 - 1.0 / (c->xi * c->xi);
+  p->cfl = c->cfl;
+  p->variant = c->variant;
+  p->vertical = c->vertical;
+  p->sum_inv_dx = 0.0;
+  for (int d = 0; d < 3; ++d) {
+    const bool act = d < c->ndim;
+    p->grav[d] = act ? c->grav[d] : 0.0;
+    p->inv_dx[d] = act ? 1.0 / c->dx[d] : 0.0;
+    p->bc[d] = act ? c->bc[d] : RSST_BC_PERIODIC;
+    if (act) p->sum_inv_dx += 1.0 / c->dx[d];
+    if (act && c->grav[d] != 0.0) p->has_grav = 1;
+  }
+}
+
+extern "C" void rsst_destroy(rsst_handle* h) {
+  if (!h) return;
+  cudaFree(h->buf[0]);
+  cudaFree(h->buf[1]);
+  cudaFree(h->d_bg);
+  cudaFree(h->d_scal);
+  cudaFree(h->d_flag);
+  cudaFree(h->d_partial);
+  cudaFree(h->d_stage);
+  cudaFreeHost(h->h_small);
+  delete h;
+}
+
+extern "C" int rsst_init(rsst_handle** out, const rsst_config* cfg, void* stream) {
+  if (!out) { rsst_set_error("handle pointer is NULL"); return RSST_EINVAL; }
+  *out = nullptr;
+  RC_TRY(validate(cfg));
+  if (cfg->precision != RSST_FP64) {
+    rsst_set_error("precision %d not available in this build", cfg->precision);
+    return RSST_EUNSUPPORTED;
+  }
+  rsst_handle* h = new rsst_handle();
+  memset(h, 0, sizeof *h);
+  h->cfg = *cfg;
+  h->cfg.bg_rho = nullptr;
+  h->cfg.bg_p = nullptr;
+  h->stream = (cudaStream_t)stream;
+  h->elem = sizeof(double);
+  make_geom(cfg, h->elem, &h->g);
+  make_phys(cfg, &h->p);
+  const int nv = cfg->ndim + 2;
+  const size_t sbytes = (size_t)nv * h->g.fstride * h->elem;
+  int rc = RSST_OK;
+#define ALLOC(ptr, bytes)                                                          \
+  if (cudaMalloc((void**)&(ptr), (bytes)) != cudaSuccess) {                        \
+    cudaGetLastError();                                                            \
+    rsst_set_error("cudaMalloc of %zu bytes failed", (size_t)(bytes));             \
+    rc = RSST_ENOMEM;                                                              \
+    goto fail;                                                                     \
+  }
+  ALLOC(h->buf[0], sbytes);
+  ALLOC(h->buf[1], sbytes);
+  ALLOC(h->d_scal, 16 * sizeof(double));
+  ALLOC(h->d_flag, sizeof(unsigned int));
+  ALLOC(h->d_partial, (size_t)nv * 1024 * sizeof(double));
+  ALLOC(h->d_stage, (size_t)nv * h->g.ncells * sizeof(double));
+  if (cudaMallocHost((void**)&h->h_small, 64 * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    rsst_set_error("cudaMallocHost failed");
+    rc = RSST_ENOMEM;
+    goto fail;
+  }
+  if (cfg->vertical >= 0) {
+    const int nvert = h->g.n[cfg->vertical];
+    h->bg_len = nvert + 2 * RSST_G;
+    double* tmp = (double*)malloc(2 * h->bg_len * sizeof(double));
+    for (int k = 0; k < h->bg_len; ++k) {
+      int src = k;
+      if (cfg->bc[cfg->vertical] == RSST_BC_PERIODIC) src = ((k - RSST_G) % nvert + nvert) % nvert + RSST_G;
+      tmp[k] = cfg->bg_rho[src];
+      tmp[h->bg_len + k] = cfg->bg_p[src] / (cfg->gamma - 1.0);
+    }
+    ALLOC(h->d_bg, 2 * h->bg_len * sizeof(double));
+    const cudaError_t e = cudaMemcpy(h->d_bg, tmp, 2 * h->bg_len * sizeof(double), cudaMemcpyHostToDevice);
+    free(tmp);
+    if (e != cudaSuccess) { rsst_set_error("background upload: %s", cudaGetErrorString(e)); rc = RSST_ECUDA; goto fail; }
+  }
+  if (cudaMemset(h->buf[0], 0, sbytes) != cudaSuccess || cudaMemset(h->buf[1], 0, sbytes) != cudaSuccess ||
+      cudaMemset(h->d_scal, 0, 16 * sizeof(double)) != cudaSuccess || cudaMemset(h->d_flag, 0, sizeof(unsigned)) != cudaSuccess) {
+    rsst_set_error("initial memset failed");
+    rc = RSST_ECUDA;
+    goto fail;
+  }
+#undef ALLOC
+  *out = h;
+  return RSST_OK;
+fail:
+  rsst_destroy(h);
+  return rc;
+}
+
+static int check_flag(rsst_handle* h) {
+  CUDA_TRY(cudaMemcpyAsync(h->h_small, h->d_flag, sizeof(unsigned int), cudaMemcpyDeviceToHost, h->stream));
+  CUDA_TRY(cudaStreamSynchronize(h->stream));
+  unsigned int f;
+  memcpy(&f, h->h_small, sizeof f);
+  if (f) {
+    rsst_set_error("non-physical state (rho <= 0, P <= 0 or NaN) produced");
+    return RSST_ENONPHYSICAL;
+  }
+  return RSST_OK;
+}
+
+extern "C" int rsst_set_state(rsst_handle* h, const double* U, int on_host) {
+  if (!h || !U) { rsst_set_error("NULL argument"); return RSST_EINVAL; }
+  const int nv = h->g.ndim + 2;
+  const size_t bytes = (size_t)nv * h->g.ncells * sizeof(double);
+  const double* src = U;
+  if (on_host) {
+    CUDA_TRY(cudaMemcpyAsync(h->d_stage, U, bytes, cudaMemcpyHostToDevice, h->stream));
+    src = h->d_stage;
+  }
+  RC_TRY(rsst_launch_pack_fp64(src, (double*)h->buf[0], h->g, h->p, h->d_bg, h->bg_len, h->stream));
+  CUDA_TRY(cudaMemsetAsync(h->d_flag, 0, sizeof(unsigned int), h->stream));
+  CUDA_TRY(cudaMemsetAsync(h->d_scal + h->slot, 0, sizeof(double), h->stream));
+  RC_TRY(rsst_launch_cfl_fp64((const double*)h->buf[0], h->g, h->p, h->d_scal + h->slot, h->d_flag, h->stream));
+  h->launches += 2;
+  return RSST_OK;
+}
+
+extern "C" int rsst_get_state(rsst_handle* h, double* U, int on_host) {
+  if (!h || !U) { rsst_set_error("NULL argument"); return RSST_EINVAL; }
+  const int nv = h->g.ndim + 2;
+  const size_t bytes = (size_t)nv * h->g.ncells * sizeof(double);
+  double* dst = on_host ? h->d_stage : U;
+  RC_TRY(rsst_launch_unpack_fp64((const double*)h->buf[0], dst, h->g, h->stream));
+  h->launches += 1;
+  if (on_host) CUDA_TRY(cudaMemcpyAsync(U, h->d_stage, bytes, cudaMemcpyDeviceToHost, h->stream));
+  return check_flag(h);
+}
+
+extern "C" int rsst_step(rsst_handle* h, double dt, int nsteps) {
+  if (!h) { rsst_set_error("NULL handle"); return RSST_EINVAL; }
+  if (nsteps < 0) { rsst_set_error("nsteps must be >= 0"); return RSST_EINVAL; }
+  if (!std::isfinite(dt)) { rsst_set_error("dt must be finite"); return RSST_EINVAL; }
+  StageArgs<double> a;
+  memset(&a, 0, sizeof a);
+  a.g = h->g;
+  a.p = h->p;
+  a.bg = h->d_bg;
+  a.bg_len = h->bg_len;
+  a.scal = h->d_scal;
+  a.flag = h->d_flag;
+  a.dt_fixed = dt > 0.0 ? dt : 0.0;
+  double* U = (double*)h->buf[0];
+  double* Us = (double*)h->buf[1];
+  for (int s = 0; s < nsteps; ++s) {
+    a.slot = h->slot;
+    a.stage = 1;
+    a.in = U;
+    a.base = nullptr;
+    a.out = Us;
+    RC_TRY(rsst_launch_stage_fp64(a, h->stream));
+    a.stage = 2;
+    a.in = Us;
+    a.base = U;
+    a.out = U;
+    RC_TRY(rsst_launch_stage_fp64(a, h->stream));
+    h->launches += 2;
+    h->slot ^= 1;
+  }
+  return RSST_OK;
+}
+
+extern "C" int rsst_dt(rsst_handle* h, double* dt_out) {
+  if (!h || !dt_out) { rsst_set_error("NULL argument"); return RSST_EINVAL; }
+  CUDA_TRY(cudaMemcpyAsync(h->h_small, h->d_scal + h->slot, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  CUDA_TRY(cudaStreamSynchronize(h->stream));
+  const double cmax = h->h_small[0];
+  *dt_out = h->p.cfl / cmax;
+  return check_flag(h);
+}
+
+extern "C" int rsst_sync(rsst_handle* h) {
+  if (!h) { rsst_set_error("NULL handle"); return RSST_EINVAL; }
+  return check_flag(h);
+}
+
+extern "C" int rsst_conserved_sums(rsst_handle* h, double* sums) {
+  if (!h || !sums) { rsst_set_error("NULL argument"); return RSST_EINVAL; }
+  const int nv = h->g.ndim + 2;
+  double vol = 1.0;
+  for (int d = 0; d < h->g.ndim; ++d) vol *= h->cfg.dx[d];
+  RC_TRY(rsst_launch_sums_fp64((const double*)h->buf[0], h->g, h->d_partial, h->d_scal + 8, vol, h->stream));
+  h->launches += 2;
+  CUDA_TRY(cudaMemcpyAsync(h->h_small, h->d_scal + 8, nv * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  CUDA_TRY(cudaStreamSynchronize(h->stream));
+  memcpy(sums, h->h_small, nv * sizeof(double));
+  return check_flag(h);
+}
+
+extern "C" int64_t rsst_kernel_launches(const rsst_handle* h) { return h ? h->launches : 0; }
+
+extern "C" size_t rsst_config_size(void) { return sizeof(rsst_config); }

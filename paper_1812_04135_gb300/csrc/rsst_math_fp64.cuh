@@ -1,0 +1,137 @@
+// Float64 device arithmetic of the RSST step (arXiv:1812.04135).
+//
+// Each function states the passage of the paper it computes.  Variables:
+// q = conservative state (rho, m_1..m_ND, E), ND = NV - 2 dimensions.
+#pragma once
+
+#include "rsst_internal.h"
+
+namespace rsst {
+
+// Euler flux along dimension D and the approximate RSST characteristic
+// speed c_tot = |V| + a/xi of one state (Eq. pvs_dt0; Sec. 4.2).
+template <int NV, int D>
+__device__ __forceinline__ void euler_flux(const double (&q)[NV], const Phys& p,
+                                           double (&F)[NV], double& c) {
+  constexpr int ND = NV - 2;
+  const double rho = q[0];
+  const double ir = 1.0 / rho;
+  double v[ND];
+  double v2 = 0.0;
+#pragma unroll
+  for (int e = 0; e < ND; ++e) {
+    v[e] = q[1 + e] * ir;
+    v2 += v[e] * v[e];
+  }
+  const double P = p.gm1 * (q[NV - 1] - 0.5 * rho * v2);
+  const double a = sqrt(p.gamma * P * ir);
+  c = sqrt(v2) + a * p.inv_xi;
+  F[0] = q[1 + D];
+#pragma unroll
+  for (int e = 0; e < ND; ++e) F[1 + e] = q[1 + e] * v[D] + (e == D ? P : 0.0);
+  F[NV - 1] = (q[NV - 1] + P) * v[D];
+}
+
+// Local Lax-Friedrichs flux with alpha = max(c_tot(qL), c_tot(qR)), ties to
+// the left state (Sec. 4.2, step 4).
+template <int NV, int D>
+__device__ __forceinline__ void llf_flux(const double (&qL)[NV], const double (&qR)[NV],
+                                         const Phys& p, double (&F)[NV]) {
+  double FL[NV], FR[NV], cL, cR;
+  euler_flux<NV, D>(qL, p, FL, cL);
+  euler_flux<NV, D>(qR, p, FR, cR);
+  const double alpha = (cL >= cR) ? cL : cR;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) F[k] = 0.5 * (FL[k] + FR[k]) - 0.5 * alpha * (qR[k] - qL[k]);
+}
+
+// Monotonized-central limited slope (named in Sec. 4.2): 0 if ab <= 0, else
+// the smallest in magnitude of 2a, 2b, (a+b)/2, ties in that order.
+__device__ __forceinline__ double mc_slope(double a, double b) {
+  const double aa = 2.0 * fabs(a), bb = 2.0 * fabs(b), cc = 0.5 * fabs(a + b);
+  const double s = (aa <= bb && aa <= cc) ? 2.0 * a : ((bb <= cc) ? 2.0 * b : 0.5 * (a + b));
+  return (a * b > 0.0) ? s : 0.0;
+}
+
+// Reduced tendency: dU <- dU - (1 - 1/xi^2) s r, then the external force.
+//   PVS: s = dP,   r = (1/a^2, V/a^2, (e+P+rho V^2/2)/(rho a^2))   Sec. 3.2, Eqs. pvs_dt, pvs_cons_rhs
+//   DVS: s = drho, r = (1, V, (e+P+rho V^2/2)/rho)                  App. A.1
+//   PMS: s = dP,   r = (1/a^2, 0, (e+P-rho V^2/2)/(rho a^2))        App. A.2
+//   DMS: s = drho, r = (1, 0, (e+P-rho V^2/2)/rho)                  App. A.3
+//   PD : s = dP,   r = (0, 0, 1/(gamma-1))                          App. A.4
+// with dP = (gamma-1)(V^2/2 drho - V.dm + dE) (Eq. pvs_dt_dpr, ideal gas),
+// evaluated at the cell centre of the stage state; force terms
+// (0, rho F, m.F) of App. B are added after (dP excludes them).
+template <int NV>
+__device__ __forceinline__ void rsst_rhs(const double (&q)[NV], double (&dU)[NV], const Phys& p) {
+  constexpr int ND = NV - 2;
+  const double rho = q[0];
+  if (p.variant != RSST_EULER) {
+    const double ir = 1.0 / rho;
+    double v[ND];
+    double v2 = 0.0, vdm = 0.0;
+#pragma unroll
+    for (int e = 0; e < ND; ++e) {
+      v[e] = q[1 + e] * ir;
+      v2 += v[e] * v[e];
+      vdm += v[e] * dU[1 + e];
+    }
+    const double P = p.gm1 * (q[NV - 1] - 0.5 * rho * v2);
+    const double e_int = P * p.inv_gm1;
+    const double kin = 0.5 * rho * v2;
+    double s, r0, rv, rE;  // r = (r0, rv * V, rE); rv in {0, 1/a^2, 1}
+    const int var = p.variant;
+    if (var == RSST_PVS || var == RSST_PMS || var == RSST_PD) {
+      s = p.gm1 * (0.5 * v2 * dU[0] - vdm + dU[NV - 1]);
+      if (var == RSST_PD) {
+        r0 = 0.0; rv = 0.0; rE = p.inv_gm1;
+      } else {
+        const double ia2 = rho / (p.gamma * P);  // 1/a^2
+        r0 = ia2;
+        rv = (var == RSST_PVS) ? ia2 : 0.0;
+        rE = (var == RSST_PVS ? (e_int + P + kin) : (e_int + P - kin)) * ia2 * ir;
+      }
+    } else {  // DVS, DMS
+      s = dU[0];
+      r0 = 1.0;
+      rv = (var == RSST_DVS) ? 1.0 : 0.0;
+      rE = (var == RSST_DVS ? (e_int + P + kin) : (e_int + P - kin)) * ir;
+    }
+    const double fs = p.f * s;
+    dU[0] -= fs * r0;
+#pragma unroll
+    for (int e = 0; e < ND; ++e) dU[1 + e] -= fs * (rv * v[e]);
+    dU[NV - 1] -= fs * rE;
+  }
+  if (p.has_grav) {
+    double mg = 0.0;
+#pragma unroll
+    for (int e = 0; e < ND; ++e) {
+      dU[1 + e] += rho * p.grav[e];
+      mg += q[1 + e] * p.grav[e];
+    }
+    dU[NV - 1] += mg;
+  }
+}
+
+// CFL rate sum_d c_tot/dx_d of a cell and its physical-state check.
+template <int NV>
+__device__ __forceinline__ double cfl_rate(const double (&q)[NV], const Phys& p, bool& ok) {
+  constexpr int ND = NV - 2;
+  const double rho = q[0];
+  const double ir = 1.0 / rho;
+  double v2 = 0.0;
+  bool fin = isfinite(q[0]) && isfinite(q[NV - 1]);
+#pragma unroll
+  for (int e = 0; e < ND; ++e) {
+    const double ve = q[1 + e] * ir;
+    v2 += ve * ve;
+    fin = fin && isfinite(q[1 + e]);
+  }
+  const double P = p.gm1 * (q[NV - 1] - 0.5 * rho * v2);
+  ok = fin && rho > 0.0 && P > 0.0;
+  const double c = sqrt(v2) + sqrt(p.gamma * P * ir) * p.inv_xi;
+  return c * p.sum_inv_dx;
+}
+
+}  // namespace rsst

@@ -1,0 +1,221 @@
+"""Thin Python binding of librsst (C ABI in include/rsst.h).
+
+Argument marshalling only: every step of the method runs in the CUDA
+library.  Functions keep the C names (``rsst_init``, ``rsst_step``, ...);
+``Solver`` wraps a handle for convenience.  If librsst.so is missing or
+cannot load, every call raises: there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "librsst.so")
+
+RSST_OK, RSST_EINVAL, RSST_ECUDA, RSST_ENONPHYSICAL, RSST_ETIMEOUT, RSST_EUNSUPPORTED, RSST_ENOMEM = 0, -1, -2, -3, -4, -5, -6
+ERROR_NAMES = {-1: "EINVAL", -2: "ECUDA", -3: "ENONPHYSICAL", -4: "ETIMEOUT", -5: "EUNSUPPORTED", -6: "ENOMEM"}
+VARIANTS = {"euler": 0, "dvs": 1, "pvs": 2, "dms": 3, "pms": 4, "pd": 5}
+PRECISIONS = {"fp64": 0, "fp32_pert": 1}
+BCS = {"periodic": 0, "reflect": 1}
+
+
+class RsstError(RuntimeError):
+    def __init__(self, code: int, where: str, msg: str):
+        super().__init__(f"{where}: RSST_{ERROR_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Config(C.Structure):
+    _fields_ = [
+        ("ndim", C.c_int32), ("n", C.c_int32 * 3), ("dx", C.c_double * 3), ("bc", C.c_int32 * 3),
+        ("variant", C.c_int32), ("precision", C.c_int32), ("xi", C.c_double), ("gamma", C.c_double),
+        ("cfl", C.c_double), ("grav", C.c_double * 3), ("vertical", C.c_int32), ("reserved", C.c_int32),
+        ("bg_rho", C.POINTER(C.c_double)), ("bg_p", C.POINTER(C.c_double)),
+    ]
+
+
+_lib = None
+
+
+def lib():
+    """Load librsst.so once; raise if it is absent (build it with __graft_entry__.build())."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"librsst.so not built at {LIB_PATH}; run __graft_entry__.build()")
+        L = C.CDLL(LIB_PATH)
+        vp, i32, i64, dbl = C.c_void_p, C.c_int, C.c_int64, C.c_double
+        pd = C.POINTER(C.c_double)
+        sig = {
+            "rsst_init": (i32, [C.POINTER(vp), C.POINTER(Config), vp]),
+            "rsst_destroy": (None, [vp]),
+            "rsst_set_state": (i32, [vp, vp, i32]),
+            "rsst_get_state": (i32, [vp, vp, i32]),
+            "rsst_step": (i32, [vp, dbl, i32]),
+            "rsst_dt": (i32, [vp, pd]),
+            "rsst_sync": (i32, [vp]),
+            "rsst_conserved_sums": (i32, [vp, pd]),
+            "rsst_kernel_launches": (i64, [vp]),
+            "rsst_config_size": (C.c_size_t, []),
+            "rsst_last_error": (C.c_char_p, []),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        if L.rsst_config_size() != C.sizeof(Config):
+            raise ImportError("rsst_config layout mismatch between librsst.so and the binding")
+        _lib = L
+    return _lib
+
+
+def _check(rc: int, where: str) -> int:
+    if rc != RSST_OK:
+        raise RsstError(rc, where, lib().rsst_last_error().decode(errors="replace"))
+    return rc
+
+
+def make_config(ndim, n, dx, *, variant="pvs", precision="fp64", xi=1.0, gamma=5.0 / 3.0, cfl=0.4,
+                grav=(0.0, 0.0, 0.0), bc=("periodic",) * 3, vertical=-1, bg_rho=None, bg_p=None):
+    """Build an ``rsst_config``; the returned object keeps the background arrays alive."""
+    cfg = Config()
+    cfg.ndim = int(ndim)
+    for d in range(3):
+        cfg.n[d] = int(n[d]) if d < ndim else 1
+        cfg.dx[d] = float(dx[d]) if d < ndim else 1.0
+        b = bc[d] if d < len(bc) else "periodic"
+        cfg.bc[d] = BCS[b] if isinstance(b, str) else int(b)
+        cfg.grav[d] = float(grav[d]) if d < len(grav) else 0.0
+    cfg.variant = VARIANTS[variant] if isinstance(variant, str) else int(variant)
+    cfg.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    cfg.xi, cfg.gamma, cfg.cfl = float(xi), float(gamma), float(cfl)
+    cfg.vertical = int(vertical)
+    cfg._keep = []
+    if bg_rho is not None:
+        r = np.ascontiguousarray(bg_rho, dtype=np.float64)
+        p = np.ascontiguousarray(bg_p, dtype=np.float64)
+        cfg._keep = [r, p]
+        cfg.bg_rho = r.ctypes.data_as(C.POINTER(C.c_double))
+        cfg.bg_p = p.ctypes.data_as(C.POINTER(C.c_double))
+    return cfg
+
+
+def config_from_workload(w: dict, precision="fp64", **over):
+    args = dict(variant=w["variant"], precision=precision, xi=w["xi"], gamma=w["gamma"], cfl=w.get("cfl", 0.4),
+                grav=w["grav"], bc=w["bc"], vertical=w["vertical"] if w["bg_rho"] is not None else -1,
+                bg_rho=w["bg_rho"], bg_p=w["bg_p"])
+    args.update(over)
+    return make_config(w["ndim"], w["n"], w["dx"], **args)
+
+
+def _stream_ptr(stream) -> Optional[int]:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return getattr(stream, "cuda_stream", stream)
+
+
+# --- the C entry points, same names -----------------------------------------
+
+def rsst_init(cfg: Config, stream=None) -> int:
+    h = C.c_void_p()
+    _check(lib().rsst_init(C.byref(h), C.byref(cfg), _stream_ptr(stream)), "rsst_init")
+    return h.value
+
+
+def rsst_destroy(h: int) -> None:
+    lib().rsst_destroy(h)
+
+
+def rsst_set_state(h: int, U, on_host: bool = False) -> None:
+    """U: float64 tensor or ndarray in the caller layout [nvar][nz][ny][nx], contiguous."""
+    ptr = U.ctypes.data if isinstance(U, np.ndarray) else U.data_ptr()
+    _check(lib().rsst_set_state(h, ptr, int(on_host)), "rsst_set_state")
+
+
+def rsst_get_state(h: int, U, on_host: bool = False) -> None:
+    ptr = U.ctypes.data if isinstance(U, np.ndarray) else U.data_ptr()
+    _check(lib().rsst_get_state(h, ptr, int(on_host)), "rsst_get_state")
+
+
+def rsst_step(h: int, dt: float = 0.0, nsteps: int = 1) -> None:
+    _check(lib().rsst_step(h, float(dt), int(nsteps)), "rsst_step")
+
+
+def rsst_dt(h: int) -> float:
+    out = C.c_double()
+    _check(lib().rsst_dt(h, C.byref(out)), "rsst_dt")
+    return out.value
+
+
+def rsst_sync(h: int) -> None:
+    _check(lib().rsst_sync(h), "rsst_sync")
+
+
+def rsst_conserved_sums(h: int, nvar: int) -> list:
+    out = (C.c_double * nvar)()
+    _check(lib().rsst_conserved_sums(h, out), "rsst_conserved_sums")
+    return list(out)
+
+
+def rsst_kernel_launches(h: int) -> int:
+    return int(lib().rsst_kernel_launches(h))
+
+
+class Solver:
+    """One run on the current CUDA device; state in and out as float64 torch tensors."""
+
+    def __init__(self, w: dict, precision: str = "fp64", stream=None, **over):
+        import torch
+        self.w = w
+        self.ndim = w["ndim"]
+        self.nvar = self.ndim + 2
+        self.shape = (self.nvar,) + tuple(reversed(w["n"]))
+        self.cfg = config_from_workload(w, precision=precision, **over)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.h = rsst_init(self.cfg, self.stream)
+
+    def set_state(self, U) -> None:
+        import torch
+        if isinstance(U, np.ndarray):
+            U = torch.from_numpy(np.ascontiguousarray(U, dtype=np.float64))
+        U = U.contiguous()
+        assert U.dtype == torch.float64 and tuple(U.shape) == self.shape, (U.dtype, U.shape, self.shape)
+        self._keep = U
+        rsst_set_state(self.h, U, on_host=not U.is_cuda)
+
+    def get_state(self, device="cuda"):
+        import torch
+        out = torch.empty(self.shape, dtype=torch.float64, device=device)
+        rsst_get_state(self.h, out, on_host=(out.device.type == "cpu"))
+        return out
+
+    def step(self, nsteps: int = 1, dt: float = 0.0) -> None:
+        rsst_step(self.h, dt, nsteps)
+
+    def dt(self) -> float:
+        return rsst_dt(self.h)
+
+    def sync(self) -> None:
+        rsst_sync(self.h)
+
+    def sums(self) -> list:
+        return rsst_conserved_sums(self.h, self.nvar)
+
+    def launches(self) -> int:
+        return rsst_kernel_launches(self.h)
+
+    def close(self) -> None:
+        if getattr(self, "h", None):
+            rsst_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

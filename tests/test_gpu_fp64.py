@@ -1,0 +1,188 @@
+"""Float64 CUDA path vs the CPU oracle, element by element, through the C ABI.
+
+Tolerance: relative L-infinity 1e-10 per field (tests/parity.py).  Sizes
+span several tiles with ragged tails on every axis; all forms, both wall
+types, gravity with a background, and the workloads' full sizes."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import rsst_oracle as ro
+from oracle.workload import problem_from
+from paper_1812_04135_gb300 import inputs, rsst
+from tests.parity import rel_linf
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-10
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import os
+    if not os.path.exists(rsst.LIB_PATH):
+        import __graft_entry__
+        __graft_entry__.build()
+    rsst.lib()
+    torch.cuda.init()
+
+
+def gpu_run(w, nsteps, dt=0.0, precision="fp64", **over):
+    s = rsst.Solver(w, precision, **over)
+    try:
+        s.set_state(torch.from_numpy(w["U"]).cuda())
+        s.step(nsteps, dt)
+        return s.get_state("cpu")
+    finally:
+        s.close()
+
+
+def oracle_run(w, nsteps, dt=None, **over):
+    prob, U = problem_from(w, **over)
+    return ro.run(U, prob, nsteps, dt=dt)
+
+
+def _assert_close(got, ref, gamma, tol=TOL, what=""):
+    err = rel_linf(got, ref, gamma)
+    assert max(err) < tol, (what, err)
+
+
+SIZES = {1: (300,), 2: (70, 37), 3: (35, 18, 11)}
+
+
+@pytest.mark.parametrize("ndim", [1, 2, 3])
+@pytest.mark.parametrize("var", ["euler", "dvs", "pvs", "dms", "pms", "pd"])
+def test_periodic_all_forms(ndim, var):
+    w = inputs.random_smooth_state(ndim, SIZES[ndim], xi=6.0, variant=var)
+    _assert_close(gpu_run(w, 4), oracle_run(w, 4), w["gamma"], what=(ndim, var))
+
+
+@pytest.mark.parametrize("ndim", [1, 2, 3])
+def test_reflecting_walls_and_gravity(ndim):
+    bc = ("reflect", "periodic", "reflect")[:ndim] if ndim > 1 else ("reflect",)
+    grav = (0.3, -0.8, 0.5)[:ndim] + (0.0,) * (3 - ndim)
+    for var in ("pvs", "dms"):
+        w = inputs.random_smooth_state(ndim, SIZES[ndim], xi=5.0, variant=var, bc=bc, grav=grav)
+        _assert_close(gpu_run(w, 4), oracle_run(w, 4), w["gamma"], what=(ndim, var))
+
+
+def test_stratified_background_2d():
+    w = inputs.polytrope_2d(40, 70, xi=20.0, contrast=20.0, amp=1e-2)
+    for var in ("pvs", "pms", "dvs"):
+        w["variant"] = var
+        _assert_close(gpu_run(w, 6), oracle_run(w, 6), w["gamma"], what=var)
+
+
+def test_stratified_background_3d_small():
+    w = inputs.polytrope_3d(20, 12, 18, xi=50.0, amp=1e-2)
+    _assert_close(gpu_run(w, 5), oracle_run(w, 5), w["gamma"])
+
+
+def test_fixed_dt_and_many_steps():
+    w = inputs.random_smooth_state(2, (40, 34), xi=4.0, variant="pms")
+    _assert_close(gpu_run(w, 20, dt=1e-3), oracle_run(w, 20, dt=1e-3), w["gamma"])
+    _assert_close(gpu_run(w, 50), oracle_run(w, 50), w["gamma"])
+
+
+def test_dt_matches_cfl_rule():
+    w = inputs.shear_layer_2d(64, 48, xi=30.0)
+    s = rsst.Solver(w, "fp64")
+    s.set_state(torch.from_numpy(w["U"]).cuda())
+    prob, U = problem_from(w)
+    assert s.dt() == pytest.approx(ro.cfl_dt(U, prob), rel=1e-13)
+    s.step(3)
+    U3 = ro.run(U, prob, 3)
+    assert s.dt() == pytest.approx(ro.cfl_dt(U3, prob), rel=1e-12)
+    s.close()
+
+
+def test_sound_wave_workload_1d():
+    """1D N = 256 sound eigenmode at xi = 10, 200 steps (a/xi travel)."""
+    for xi, var in ((10.0, "pvs"), (1.0, "dvs"), (10.0, "pms")):
+        w = inputs.sound_wave_1d(256, xi=xi, variant=var)
+        _assert_close(gpu_run(w, 200), oracle_run(w, 200), w["gamma"], what=(xi, var))
+
+
+def test_contact_workload_1d():
+    for xi, var in ((10.0, "pvs"), (1.0, "dvs"), (10.0, "pd")):
+        w = inputs.contact_1d(256, xi=xi, variant=var)
+        _assert_close(gpu_run(w, 10), oracle_run(w, 10), w["gamma"], what=(xi, var))
+
+
+def test_shear_layer_full_size():
+    """2D 512 x 512 shear layer, xi = 30, full-grid comparison."""
+    w = inputs.shear_layer_2d()
+    for var in ("pvs", "dvs"):
+        w["variant"] = var
+        _assert_close(gpu_run(w, 3), oracle_run(w, 3), w["gamma"], what=var)
+
+
+def test_polytrope_full_size_one_step():
+    """3D 256 x 128 x 128 stratified box, xi = 50, one step on the full grid."""
+    w = inputs.polytrope_3d()
+    _assert_close(gpu_run(w, 1), oracle_run(w, 1), w["gamma"])
+
+
+def test_momentum_conserved_to_round_off():
+    w = inputs.shear_layer_2d(256, 256, xi=30.0, variant="pms")
+    s = rsst.Solver(w, "fp64")
+    s.set_state(torch.from_numpy(w["U"]).cuda())
+    s0 = s.sums()
+    s.step(200)
+    s1 = s.sums()
+    U = torch.from_numpy(w["U"])
+    scale_m = float((U[1].abs().sum() + U[2].abs().sum())) / (256 * 256)
+    for k in (1, 2):
+        assert abs(s1[k] - s0[k]) < 1e-13 * scale_m * 200, (k, s0[k], s1[k])
+    assert abs(s1[0] - s0[0]) > 0          # PMS carries a mass source
+    s.close()
+
+
+def test_mass_conserved_dms():
+    w = inputs.shear_layer_2d(256, 128, xi=30.0, variant="dms")
+    s = rsst.Solver(w, "fp64")
+    s.set_state(torch.from_numpy(w["U"]).cuda())
+    s0 = s.sums()
+    s.step(200)
+    s1 = s.sums()
+    assert abs(s1[0] - s0[0]) < 1e-13 * abs(s0[0]) * 10
+    s.close()
+
+
+def test_sums_match_exact_sums():
+    w = inputs.random_smooth_state(3, (33, 17, 9), xi=3.0)
+    s = rsst.Solver(w, "fp64")
+    s.set_state(torch.from_numpy(w["U"]).cuda())
+    got = s.sums()
+    prob, U = problem_from(w)
+    want = ro.conserved_sums(U, prob)
+    for g, e, k in zip(got, want, range(5)):
+        assert g == pytest.approx(e, rel=1e-13, abs=1e-15), k
+    s.close()
+
+
+def test_nonphysical_state_is_flagged():
+    """The ratio-10 contact cannot run the density-reduced form at xi = 10
+    (Sec. 2.2): the step must report RSST_ENONPHYSICAL, not crash."""
+    w = inputs.contact_1d(256, xi=10.0, variant="dvs")
+    s = rsst.Solver(w, "fp64")
+    s.set_state(torch.from_numpy(w["U"]).cuda())
+    s.step(3)
+    with pytest.raises(rsst.RsstError) as e:
+        s.sync()
+    assert e.value.code == rsst.RSST_ENONPHYSICAL
+    # a fresh state clears the flag
+    w2 = inputs.contact_1d(256, xi=10.0, variant="pvs")
+    s.set_state(torch.from_numpy(w2["U"]).cuda())
+    s.sync()
+    s.close()
+
+
+def test_host_buffers_roundtrip():
+    w = inputs.random_smooth_state(2, (50, 20), xi=3.0)
+    s = rsst.Solver(w, "fp64")
+    s.set_state(torch.from_numpy(w["U"]).pin_memory())
+    got = s.get_state("cpu")
+    assert torch.equal(got, torch.from_numpy(w["U"]))
+    s.close()
