@@ -51,10 +51,10 @@ def _peaks():
 
 
 def fp64_peak_tflops(sm_mhz: float) -> float:
-    """GB300 float64 rate from unit counts and clock: 152 SMs x 1 DFMA per SM
-    per clock (2 flops) x clock; the unit count is the one the FP64 probe
-    measured."""
-    return 152 * 1.0 * 2.0 * sm_mhz * 1e6 / 1e12
+    """GB300 float64 rate from unit counts and clock: 152 SMs x 2 DFMA per SM
+    per clock (2 flops each) x clock; the unit count is the one the FP64
+    FMA probe measured."""
+    return 152 * 2.0 * 2.0 * sm_mhz * 1e6 / 1e12
 
 
 class ClockSampler:
@@ -264,7 +264,7 @@ def run_gpu(args, world, rank, local):
             "config": _config(args, w),
             "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": peak_tf, "unit": "TFLOP/s",
                          "frac": achieved_tf / peak_tf, "traffic": None,
-                         "peak_source": f"float64: 152 SMs x 2 flop/clk x {sm_mhz:.0f} MHz (unit count measured)",
+                         "peak_source": f"float64: 152 SMs x 2 DFMA/clk x 2 flop x {sm_mhz:.0f} MHz (unit count measured)",
                          "hbm_achieved_gbs": alg_bytes / launch_s / 1e9, "hbm_peak_gbs": peaks["hbm_gbs"],
                          "hbm_frac": alg_bytes / launch_s / 1e9 / peaks["hbm_gbs"], "hbm_peak_source": src},
             "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},

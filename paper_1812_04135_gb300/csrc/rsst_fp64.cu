@@ -266,7 +266,8 @@ __global__ void pack_fp64_kernel(const double* __restrict__ src, double* __restr
                       g.ndim >= 3 ? (int)(id / ((int64_t)ex * ey)) - RSST_G : 0};
     int s[3] = {c[0], c[1], c[2]};
     double sign[3] = {1.0, 1.0, 1.0};
-    int vimg = -1, vgh = -1;
+    int vimg = 0, vgh = 0;
+    bool vmirror = false;
     for (int d = 0; d < g.ndim; ++d) {
       const int n = g.n[d];
       if (s[d] >= 0 && s[d] < n) continue;
@@ -274,7 +275,7 @@ __global__ void pack_fp64_kernel(const double* __restrict__ src, double* __restr
         s[d] = (s[d] + n) % n;
       } else {
         const int img = s[d] < 0 ? -1 - s[d] : 2 * n - 1 - s[d];
-        if (d == p.vertical) { vgh = s[d]; vimg = img; }
+        if (d == p.vertical) { vgh = s[d]; vimg = img; vmirror = true; }
         s[d] = img;
         sign[d] = -1.0;
       }
@@ -284,7 +285,7 @@ __global__ void pack_fp64_kernel(const double* __restrict__ src, double* __restr
     for (int v = 0; v < nv; ++v) {
       double w = src[v * g.ncells + si];
       if (v >= 1 && v <= g.ndim) w *= sign[v - 1];
-      if (bg != nullptr && vgh != -1 && (v == 0 || v == nv - 1)) {
+      if (bg != nullptr && vmirror && (v == 0 || v == nv - 1)) {
         const double* row = bg + (v == 0 ? 0 : bg_len);
         w += row[vgh + RSST_G] - row[vimg + RSST_G];
       }
