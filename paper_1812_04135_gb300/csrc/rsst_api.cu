@@ -48,6 +48,8 @@ struct rsst_handle {
   double* d_partial;    // sums partials
   double* d_stage;      // caller-layout staging for host transfers
   double* h_small;      // pinned host scratch for small read-backs
+  float* d_tab;         // background tables (float32 mode), or null
+  PhysF pf;
   int slot;
   int64_t launches;
 };
@@ -90,6 +92,20 @@ static void make_geom(const rsst_config* c, size_t elem, Geom* g) {
   g->ncells = (int64_t)g->n[0] * g->n[1] * g->n[2];
 }
 
+static void make_physf(const Phys* p, PhysF* f) {
+  memset(f, 0, sizeof *f);
+  f->gamma = (float)p->gamma;
+  f->gm1 = (float)p->gm1;
+  f->inv_gm1 = (float)p->inv_gm1;
+  f->inv_xi = (float)p->inv_xi;
+  f->f = (float)p->f;
+  for (int d = 0; d < 3; ++d) {
+    f->grav[d] = (float)p->grav[d];
+    f->inv_dx[d] = (float)p->inv_dx[d];
+  }
+  f->sum_inv_dx = (float)p->sum_inv_dx;
+}
+
 static void make_phys(const rsst_config* c, Phys* p) {
   memset(p, 0, sizeof *p);
   p->gamma = c->gamma;
@@ -121,6 +137,7 @@ extern "C" void rsst_destroy(rsst_handle* h) {
   cudaFree(h->d_flag);
   cudaFree(h->d_partial);
   cudaFree(h->d_stage);
+  cudaFree(h->d_tab);
   cudaFreeHost(h->h_small);
   delete h;
 }
@@ -129,19 +146,16 @@ extern "C" int rsst_init(rsst_handle** out, const rsst_config* cfg, void* stream
   if (!out) { rsst_set_error("handle pointer is NULL"); return RSST_EINVAL; }
   *out = nullptr;
   RC_TRY(validate(cfg));
-  if (cfg->precision != RSST_FP64) {
-    rsst_set_error("precision %d not available in this build", cfg->precision);
-    return RSST_EUNSUPPORTED;
-  }
   rsst_handle* h = new rsst_handle();
   memset(h, 0, sizeof *h);
   h->cfg = *cfg;
   h->cfg.bg_rho = nullptr;
   h->cfg.bg_p = nullptr;
   h->stream = (cudaStream_t)stream;
-  h->elem = sizeof(double);
+  h->elem = cfg->precision == RSST_FP64 ? sizeof(double) : sizeof(float);
   make_geom(cfg, h->elem, &h->g);
   make_phys(cfg, &h->p);
+  make_physf(&h->p, &h->pf);
   const int nv = cfg->ndim + 2;
   const size_t sbytes = (size_t)nv * h->g.fstride * h->elem;
   int rc = RSST_OK;
@@ -178,6 +192,12 @@ extern "C" int rsst_init(rsst_handle** out, const rsst_config* cfg, void* stream
     const cudaError_t e = cudaMemcpy(h->d_bg, tmp, 2 * h->bg_len * sizeof(double), cudaMemcpyHostToDevice);
     free(tmp);
     if (e != cudaSuccess) { rsst_set_error("background upload: %s", cudaGetErrorString(e)); rc = RSST_ECUDA; goto fail; }
+    if (cfg->precision == RSST_FP32_PERT) {
+      ALLOC(h->d_tab, (size_t)TB_COUNT * h->bg_len * sizeof(float));
+      rc = rsst_launch_bgtab(h->d_bg, h->bg_len, h->g, h->p, h->d_tab, 0);
+      if (rc != RSST_OK) goto fail;
+      if (cudaDeviceSynchronize() != cudaSuccess) { rsst_set_error("background table kernel failed"); rc = RSST_ECUDA; goto fail; }
+    }
   }
   if (cudaMemset(h->buf[0], 0, sbytes) != cudaSuccess || cudaMemset(h->buf[1], 0, sbytes) != cudaSuccess ||
       cudaMemset(h->d_scal, 0, 16 * sizeof(double)) != cudaSuccess || cudaMemset(h->d_flag, 0, sizeof(unsigned)) != cudaSuccess) {
@@ -214,10 +234,18 @@ extern "C" int rsst_set_state(rsst_handle* h, const double* U, int on_host) {
     CUDA_TRY(cudaMemcpyAsync(h->d_stage, U, bytes, cudaMemcpyHostToDevice, h->stream));
     src = h->d_stage;
   }
-  RC_TRY(rsst_launch_pack_fp64(src, (double*)h->buf[0], h->g, h->p, h->d_bg, h->bg_len, h->stream));
+  const bool f32 = h->cfg.precision == RSST_FP32_PERT;
+  if (f32)
+    RC_TRY(rsst_launch_pack_fp32(src, (float*)h->buf[0], h->g, h->p, h->d_bg, h->bg_len, h->stream));
+  else
+    RC_TRY(rsst_launch_pack_fp64(src, (double*)h->buf[0], h->g, h->p, h->d_bg, h->bg_len, h->stream));
   CUDA_TRY(cudaMemsetAsync(h->d_flag, 0, sizeof(unsigned int), h->stream));
   CUDA_TRY(cudaMemsetAsync(h->d_scal + h->slot, 0, sizeof(double), h->stream));
-  RC_TRY(rsst_launch_cfl_fp64((const double*)h->buf[0], h->g, h->p, h->d_scal + h->slot, h->d_flag, h->stream));
+  if (f32)
+    RC_TRY(rsst_launch_cfl_fp32((const float*)h->buf[0], h->g, h->p, h->pf, h->d_tab, h->bg_len, h->d_scal + h->slot,
+                                h->d_flag, h->stream));
+  else
+    RC_TRY(rsst_launch_cfl_fp64((const double*)h->buf[0], h->g, h->p, h->d_scal + h->slot, h->d_flag, h->stream));
   h->launches += 2;
   return RSST_OK;
 }
@@ -227,43 +255,57 @@ extern "C" int rsst_get_state(rsst_handle* h, double* U, int on_host) {
   const int nv = h->g.ndim + 2;
   const size_t bytes = (size_t)nv * h->g.ncells * sizeof(double);
   double* dst = on_host ? h->d_stage : U;
-  RC_TRY(rsst_launch_unpack_fp64((const double*)h->buf[0], dst, h->g, h->stream));
+  if (h->cfg.precision == RSST_FP32_PERT)
+    RC_TRY(rsst_launch_unpack_fp32((const float*)h->buf[0], dst, h->g, h->p, h->d_bg, h->bg_len, h->stream));
+  else
+    RC_TRY(rsst_launch_unpack_fp64((const double*)h->buf[0], dst, h->g, h->stream));
   h->launches += 1;
   if (on_host) CUDA_TRY(cudaMemcpyAsync(U, h->d_stage, bytes, cudaMemcpyDeviceToHost, h->stream));
   return check_flag(h);
 }
 
-extern "C" int rsst_step(rsst_handle* h, double dt, int nsteps) {
-  if (!h) { rsst_set_error("NULL handle"); return RSST_EINVAL; }
-  if (nsteps < 0) { rsst_set_error("nsteps must be >= 0"); return RSST_EINVAL; }
-  if (!std::isfinite(dt)) { rsst_set_error("dt must be finite"); return RSST_EINVAL; }
-  StageArgs<double> a;
+template <typename T>
+static int run_steps(rsst_handle* h, double dt, int nsteps) {
+  StageArgs<T> a;
   memset(&a, 0, sizeof a);
   a.g = h->g;
   a.p = h->p;
+  a.pf = h->pf;
   a.bg = h->d_bg;
   a.bg_len = h->bg_len;
+  a.tab = h->d_tab;
+  a.tab_len = h->bg_len;
   a.scal = h->d_scal;
   a.flag = h->d_flag;
   a.dt_fixed = dt > 0.0 ? dt : 0.0;
-  double* U = (double*)h->buf[0];
-  double* Us = (double*)h->buf[1];
+  T* U = (T*)h->buf[0];
+  T* Us = (T*)h->buf[1];
   for (int s = 0; s < nsteps; ++s) {
     a.slot = h->slot;
     a.stage = 1;
     a.in = U;
     a.base = nullptr;
     a.out = Us;
-    RC_TRY(rsst_launch_stage_fp64(a, h->stream));
+    if constexpr (sizeof(T) == 8) RC_TRY(rsst_launch_stage_fp64(a, h->stream));
+    else RC_TRY(rsst_launch_stage_fp32(a, h->stream));
     a.stage = 2;
     a.in = Us;
     a.base = U;
     a.out = U;
-    RC_TRY(rsst_launch_stage_fp64(a, h->stream));
+    if constexpr (sizeof(T) == 8) RC_TRY(rsst_launch_stage_fp64(a, h->stream));
+    else RC_TRY(rsst_launch_stage_fp32(a, h->stream));
     h->launches += 2;
     h->slot ^= 1;
   }
   return RSST_OK;
+}
+
+extern "C" int rsst_step(rsst_handle* h, double dt, int nsteps) {
+  if (!h) { rsst_set_error("NULL handle"); return RSST_EINVAL; }
+  if (nsteps < 0) { rsst_set_error("nsteps must be >= 0"); return RSST_EINVAL; }
+  if (!std::isfinite(dt)) { rsst_set_error("dt must be finite"); return RSST_EINVAL; }
+  if (h->cfg.precision == RSST_FP32_PERT) return run_steps<float>(h, dt, nsteps);
+  return run_steps<double>(h, dt, nsteps);
 }
 
 extern "C" int rsst_dt(rsst_handle* h, double* dt_out) {
@@ -285,7 +327,11 @@ extern "C" int rsst_conserved_sums(rsst_handle* h, double* sums) {
   const int nv = h->g.ndim + 2;
   double vol = 1.0;
   for (int d = 0; d < h->g.ndim; ++d) vol *= h->cfg.dx[d];
-  RC_TRY(rsst_launch_sums_fp64((const double*)h->buf[0], h->g, h->d_partial, h->d_scal + 8, vol, h->stream));
+  if (h->cfg.precision == RSST_FP32_PERT)
+    RC_TRY(rsst_launch_sums_fp32((const float*)h->buf[0], h->g, h->p, h->d_bg, h->bg_len, h->d_partial, h->d_scal + 8,
+                                 vol, h->stream));
+  else
+    RC_TRY(rsst_launch_sums_fp64((const double*)h->buf[0], h->g, h->d_partial, h->d_scal + 8, vol, h->stream));
   h->launches += 2;
   CUDA_TRY(cudaMemcpyAsync(h->h_small, h->d_scal + 8, nv * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
   CUDA_TRY(cudaStreamSynchronize(h->stream));

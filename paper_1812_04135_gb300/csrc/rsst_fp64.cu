@@ -15,14 +15,11 @@
 //      maximum for the next step and the physical-state flag.
 #include <cstdio>
 
+#include "rsst_common.cuh"
 #include "rsst_internal.h"
 #include "rsst_math_fp64.cuh"
 
 namespace rsst {
-
-__device__ __forceinline__ int64_t pidx(const Geom& g, int i, int j, int k) {
-  return (int64_t)(k + g.gz) * g.plane + (int64_t)(j + g.gy) * g.pitch + (i + g.xoff);
-}
 
 // Store a cell and the edge ghost cells that mirror or wrap it.
 template <int NV>
@@ -64,29 +61,6 @@ __device__ __forceinline__ void store_with_ghosts(double* __restrict__ out, cons
 #pragma unroll
       for (int v = 0; v < NV; ++v) out[v * fs + og] = w[v];
     }
-  }
-}
-
-__device__ __forceinline__ double warp_max(double x) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) x = fmax(x, __shfl_xor_sync(0xffffffffu, x, o));
-  return x;
-}
-
-// Block-wide maximum of non-negative values, then one atomicMax on the bit
-// pattern (monotone for non-negative doubles).
-template <int NT>
-__device__ __forceinline__ void block_max_to(double x, double* dst, double* sred) {
-  x = warp_max(x);
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  __syncthreads();
-  if (lane == 0) sred[wid] = x;
-  __syncthreads();
-  if (wid == 0) {
-    double y = lane < NT / 32 ? sred[lane] : 0.0;
-    y = warp_max(y);
-    if (lane == 0 && y > 0.0)
-      atomicMax(reinterpret_cast<unsigned long long*>(dst), (unsigned long long)__double_as_longlong(y));
   }
 }
 

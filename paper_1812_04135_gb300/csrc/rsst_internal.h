@@ -39,6 +39,33 @@ struct Phys {
   int has_grav;
 };
 
+// Float32 copies of the constants used by the float32 kernels.
+struct PhysF {
+  float gamma, gm1, inv_gm1, inv_xi, f;
+  float grav[3];
+  float inv_dx[3];
+  float sum_inv_dx;
+};
+
+// Background tables of the float32 perturbation mode: float32 rows of
+// length tab_len (= padded vertical index k = interior index + 2), computed
+// in float64 on the device at set-up.  Face entries at index k describe the
+// face between padded cells k-1 and k.
+enum BgTab {
+  TB_RHO0 = 0, TB_E0, TB_P0, TB_H0,                 // cell background, H0 = E0 + P0
+  TB_R0,                                             // 5 rows: background residual L(U0) incl. force
+  TB_D0RHO = TB_R0 + 5, TB_D0MV, TB_D0E,             // background Euler tendency (rho, m_vert, E)
+  TB_S = TB_D0E + 1,                                 // slope rows, 2 components (rho, E) x 6:
+                                                     //   d0L, d0R, then lin_B(d0) - MC(d0) for B = 0, 2a, 2b, c
+  TB_F = TB_S + 12,                                  // face rows:
+  TB_FRHOL = TB_F, TB_FRHOR, TB_FEL, TB_FER, TB_FPL, TB_FPR, TB_FHL, TB_FHR,
+  TB_FAL, TB_FAR,                                    // background sound speeds a0 left / right
+  TB_FG,                                             // c0L - c0R
+  TB_FALPHA,                                         // alpha0 = max(c0L, c0R)
+  TB_FDRHO, TB_FDE,                                  // U0R - U0L (rho, E)
+  TB_COUNT
+};
+
 // Arguments of one fused RK stage launch (single run).
 template <typename T>
 struct StageArgs {
@@ -54,6 +81,9 @@ struct StageArgs {
   int slot;         // CFL slot read this step (stage 2 writes slot ^ 1)
   int stage;        // 1 or 2
   double dt_fixed;  // > 0: fixed step
+  PhysF pf;         // float32 constants (float32 kernels)
+  const float* tab; // background tables [TB_COUNT][tab_len] (float32 mode), or null
+  int tab_len;
 };
 
 // Host-side launchers (defined in the .cu files).
@@ -65,5 +95,16 @@ int rsst_launch_cfl_fp64(const double* U, const Geom& g, const Phys& p, double* 
                          unsigned int* flag, cudaStream_t s);
 int rsst_launch_sums_fp64(const double* U, const Geom& g, double* partial, double* out,
                           double scale, cudaStream_t s);
+
+int rsst_launch_stage_fp32(const StageArgs<float>& a, cudaStream_t s);
+int rsst_launch_bgtab(const double* bg, int bg_len, const Geom& g, const Phys& p, float* tab, cudaStream_t s);
+int rsst_launch_pack_fp32(const double* src, float* dst, const Geom& g, const Phys& p, const double* bg,
+                          int bg_len, cudaStream_t s);
+int rsst_launch_unpack_fp32(const float* src, double* dst, const Geom& g, const Phys& p, const double* bg,
+                            int bg_len, cudaStream_t s);
+int rsst_launch_cfl_fp32(const float* U, const Geom& g, const Phys& p, const PhysF& pf, const float* tab,
+                         int tab_len, double* slot_ptr, unsigned int* flag, cudaStream_t s);
+int rsst_launch_sums_fp32(const float* U, const Geom& g, const Phys& p, const double* bg, int bg_len,
+                          double* partial, double* out, double scale, cudaStream_t s);
 
 void rsst_set_error(const char* fmt, ...);

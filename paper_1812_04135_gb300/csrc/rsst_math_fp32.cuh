@@ -1,0 +1,94 @@
+// Float32 perturbation arithmetic of the RSST step.
+//
+// The state is U = U0 + U1 with U0 = (rho0, 0, E0) a float64 background that
+// depends only on the vertical index and U1 the float32 perturbation.  Every
+// quantity that feeds an update is formed from perturbation-sized terms, so
+// the low-Mach pressure and density perturbations are not lost to
+// cancellation against the background:
+//   P1 = P - P0 = (gamma-1)(E1 - |m|^2/(2 rho))                 (m0 = 0)
+//   F(U) - F(U0) = (m_D, m v_D + P1 e_D, (E0 + P0 + E1 + P1) v_D)
+//   a^2 - a0^2 = gamma (P1 rho0 - P0 rho1) / (rho rho0)
+// Faces across the vertical axis also carry the background's own face jump
+// U0R - U0L and its LLF speed alpha0; their contribution is split as
+//   alpha (U1R - U1L) + (alpha - alpha0)(U0R - U0L)
+// with alpha - alpha0 formed from c - c0 on each side and the float64
+// background difference g = c0L - c0R.  The MC slope of a component whose
+// background varies is lin_B(d1) + [lin_B(d0) - MC(d0)], where B is the
+// branch MC takes on the full differences d = d0 + d1 and the bracket is a
+// float64 table entry per branch.
+#pragma once
+
+#include "rsst_internal.h"
+
+namespace rsst {
+
+// Monotonized-central slope (Sec. 4.2), float32.
+__device__ __forceinline__ float mc_slope_f(float a, float b) {
+  const float aa = 2.0f * fabsf(a), bb = 2.0f * fabsf(b), cc = 0.5f * fabsf(a + b);
+  const float s = (aa <= bb && aa <= cc) ? 2.0f * a : ((bb <= cc) ? 2.0f * b : 0.5f * (a + b));
+  return (a * b > 0.0f) ? s : 0.0f;
+}
+
+// Branch of the MC slope: 0 -> 0, 1 -> 2a, 2 -> 2b, 3 -> (a+b)/2.
+__device__ __forceinline__ int mc_branch_f(float a, float b) {
+  if (!(a * b > 0.0f)) return 0;
+  const float aa = 2.0f * fabsf(a), bb = 2.0f * fabsf(b), cc = 0.5f * fabsf(a + b);
+  return (aa <= bb && aa <= cc) ? 1 : ((bb <= cc) ? 2 : 3);
+}
+
+__device__ __forceinline__ float mc_linear_f(int br, float a, float b) {
+  return br == 0 ? 0.0f : (br == 1 ? 2.0f * a : (br == 2 ? 2.0f * b : 0.5f * (a + b)));
+}
+
+// Full-state Euler flux and c_tot along D in float32 (no background).
+template <int NV, int D>
+__device__ __forceinline__ void euler_flux_f(const float (&q)[NV], const PhysF& p, float (&F)[NV], float& c) {
+  constexpr int ND = NV - 2;
+  const float rho = q[0];
+  const float ir = 1.0f / rho;
+  float v[ND];
+  float v2 = 0.0f;
+#pragma unroll
+  for (int e = 0; e < ND; ++e) {
+    v[e] = q[1 + e] * ir;
+    v2 += v[e] * v[e];
+  }
+  const float P = p.gm1 * (q[NV - 1] - 0.5f * rho * v2);
+  c = sqrtf(v2) + sqrtf(p.gamma * P * ir) * p.inv_xi;
+  F[0] = q[1 + D];
+#pragma unroll
+  for (int e = 0; e < ND; ++e) F[1 + e] = q[1 + e] * v[D] + (e == D ? P : 0.0f);
+  F[NV - 1] = (q[NV - 1] + P) * v[D];
+}
+
+// Perturbation flux F(U0 + q1) - F(U0) along D, the full c_tot, and c - c0.
+// Background face values: rho0, E0, P0 = (gamma-1) E0, H0 = E0 + P0, a0.
+template <int NV, int D, bool WANT_DC>
+__device__ __forceinline__ void pert_flux_f(const float (&q1)[NV], float rho0, float P0, float H0, float a0,
+                                            const PhysF& p, float (&F)[NV], float& c, float& dc) {
+  constexpr int ND = NV - 2;
+  const float rho = rho0 + q1[0];
+  const float ir = 1.0f / rho;
+  float v[ND];
+  float v2 = 0.0f, mv = 0.0f;
+#pragma unroll
+  for (int e = 0; e < ND; ++e) {
+    v[e] = q1[1 + e] * ir;
+    v2 += v[e] * v[e];
+    mv += q1[1 + e] * v[e];
+  }
+  const float P1 = p.gm1 * (q1[NV - 1] - 0.5f * mv);
+  const float a = sqrtf(p.gamma * (P0 + P1) * ir);
+  const float vm = sqrtf(v2);
+  c = vm + a * p.inv_xi;
+  if (WANT_DC) {
+    const float da2 = p.gamma * (P1 * rho0 - P0 * q1[0]) * ir / rho0;
+    dc = vm + (da2 / (a + a0)) * p.inv_xi;
+  }
+  F[0] = q1[1 + D];
+#pragma unroll
+  for (int e = 0; e < ND; ++e) F[1 + e] = q1[1 + e] * v[D] + (e == D ? P1 : 0.0f);
+  F[NV - 1] = (H0 + q1[NV - 1] + P1) * v[D];
+}
+
+}  // namespace rsst

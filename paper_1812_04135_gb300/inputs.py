@@ -151,6 +151,8 @@ def polytrope_profile(z: np.ndarray, contrast: float, index: float = 1.5, g: flo
     rho = (theta/theta_t)^n, so rho(0)/rho(1) = contrast; returns (rho, P)."""
     theta_t = g / (index + 1.0) / (contrast ** (1.0 / index) - 1.0)
     theta = theta_t + g * (1.0 - z) / (index + 1.0)
+    if np.any(theta <= 0.0):
+        raise ValueError("polytrope temperature <= 0 at a ghost cell: grid too coarse for this contrast")
     rho = (theta / theta_t) ** index
     return rho, rho * theta
 

@@ -24,3 +24,45 @@ def rel_linf(got: torch.Tensor, ref: torch.Tensor, gamma: float):
     ref = ref.double().cpu()
     sc = field_scales(ref, gamma)
     return [float((got[k] - ref[k]).abs().max()) / sc[k] for k in range(ref.shape[0])]
+
+
+_ORACLE_CACHE = {}
+
+
+def oracle_cached(key, fn):
+    """Memoise an expensive oracle result within one test process."""
+    if key not in _ORACLE_CACHE:
+        _ORACLE_CACHE[key] = fn()
+    return _ORACLE_CACHE[key]
+
+
+def background_state(w) -> torch.Tensor:
+    """U0 = (rho0, 0, P0/(gamma-1)) of a workload's background, broadcast to its grid."""
+    nd = w["ndim"]
+    shape = tuple(reversed(w["n"]))
+    U0 = torch.zeros((nd + 2,) + shape, dtype=torch.float64)
+    if w["bg_rho"] is None:
+        return U0
+    v = w["vertical"]
+    nv = w["n"][v]
+    r0 = torch.as_tensor(w["bg_rho"][2:2 + nv], dtype=torch.float64)
+    e0 = torch.as_tensor(w["bg_p"][2:2 + nv], dtype=torch.float64) / (w["gamma"] - 1.0)
+    ax = nd - 1 - v
+    view = [1] * nd
+    view[ax] = nv
+    U0[0] = r0.reshape(view).expand(shape)
+    U0[-1] = e0.reshape(view).expand(shape)
+    return U0
+
+
+def rel_linf_pert(got, ref, w):
+    """Per-field max |gpu - ref| over max |ref - U0|: the error relative to the
+    perturbation about the background (what the float32 mode must keep)."""
+    U0 = background_state(w)
+    got = got.double().cpu()
+    ref = ref.double().cpu()
+    out = []
+    for k in range(ref.shape[0]):
+        den = float((ref[k] - U0[k]).abs().max())
+        out.append(float((got[k] - ref[k]).abs().max()) / den if den > 0 else float("inf"))
+    return out

@@ -1,0 +1,116 @@
+"""Float32-perturbation CUDA path vs the float64 CPU oracle through the C ABI.
+
+Tolerance: relative L-infinity 1e-5 per field (tests/parity.py scales).
+Stratified cases also bound the error relative to the perturbation about
+the background, which plain float32 storage of the full state would lose
+to cancellation."""
+import pytest
+import torch
+
+from oracle import rsst_oracle as ro
+from oracle.workload import problem_from
+from paper_1812_04135_gb300 import inputs, rsst
+from tests.parity import oracle_cached, rel_linf, rel_linf_pert
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import os
+    if not os.path.exists(rsst.LIB_PATH):
+        import __graft_entry__
+        __graft_entry__.build()
+    rsst.lib()
+
+
+def gpu_run(w, nsteps, dt=0.0, precision="fp32_pert"):
+    s = rsst.Solver(w, precision)
+    try:
+        s.set_state(torch.from_numpy(w["U"]).cuda())
+        s.step(nsteps, dt)
+        return s.get_state("cpu")
+    finally:
+        s.close()
+
+
+def oracle_run(w, nsteps, dt=None):
+    prob, U = problem_from(w)
+    return ro.run(U, prob, nsteps, dt=dt)
+
+
+def check(w, nsteps, tol=TOL, pert_tol=None, what=""):
+    got = gpu_run(w, nsteps)
+    ref = oracle_run(w, nsteps)
+    err = rel_linf(got, ref, w["gamma"])
+    assert max(err) < tol, (what, err)
+    if pert_tol is not None:
+        ep = rel_linf_pert(got, ref, w)
+        assert max(ep) < pert_tol, (what, ep)
+    return err
+
+
+def test_roundtrip_keeps_float64_background():
+    """Set/get: the background stays float64, only the perturbation is rounded."""
+    w = inputs.polytrope_2d(16, 64, xi=20.0, contrast=20.0, amp=1e-3)
+    s = rsst.Solver(w, "fp32_pert")
+    U = torch.from_numpy(w["U"])
+    s.set_state(U.cuda())
+    got = s.get_state("cpu")
+    s.close()
+    pert = (U[0] - torch.from_numpy(w["bg_rho"][2:-2])[:, None]).abs().max()
+    assert float((got - U).abs().max()) <= 1e-7 * float(pert) * 2
+
+
+@pytest.mark.parametrize("ndim", [1, 2, 3])
+def test_plain_float32_storage(ndim):
+    n = {1: (300,), 2: (70, 37), 3: (35, 18, 11)}[ndim]
+    for var in ("pvs", "dms"):
+        w = inputs.random_smooth_state(ndim, n, xi=6.0, variant=var)
+        check(w, 4, what=(ndim, var))
+
+
+def test_shear_layer_with_background():
+    w = inputs.shear_layer_2d(96, 80, xi=30.0)
+    for var in ("pvs", "dvs", "pms"):
+        w["variant"] = var
+        check(w, 10, what=var)
+
+
+def test_stratified_2d_perturbation_accuracy():
+    w = inputs.polytrope_2d(40, 70, xi=20.0, contrast=20.0, amp=1e-3)
+    for var in ("pvs", "pms", "dms"):
+        w["variant"] = var
+        check(w, 10, pert_tol=2e-3, what=var)
+
+
+def test_stratified_3d_small():
+    w = inputs.polytrope_3d(20, 12, 40, xi=50.0, amp=1e-3, contrast=20.0)
+    check(w, 5, pert_tol=2e-3)
+
+
+def test_polytrope_full_size_one_step():
+    """3D 256 x 128 x 128, contrast 100, xi = 50: one step on the full grid."""
+    w = inputs.polytrope_3d()
+    got = gpu_run(w, 1)
+    ref = oracle_cached("polytrope_3d_1", lambda: oracle_run(w, 1))
+    err = rel_linf(got, ref, w["gamma"])
+    ep = rel_linf_pert(got, ref, w)
+    print("polytrope_3d fp32_pert per-field rel err", err, "vs perturbation", ep)
+    assert max(err) < TOL, err
+    assert max(ep) < 2e-3, ep
+
+
+def test_hydrostatic_background_residual_matches_oracle():
+    """With no perturbation the float32 state evolves only by the float64
+    background residual L(U0): compare after 3 steps relative to that drift."""
+    w = inputs.polytrope_2d(16, 64, xi=20.0, contrast=20.0, amp=0.0)
+    check(w, 3, pert_tol=1e-4)
+
+
+def test_sound_wave_and_contact_1d():
+    w = inputs.sound_wave_1d(256, xi=10.0, variant="pvs")
+    check(w, 100)
+    w = inputs.contact_1d(256, xi=10.0, variant="pvs")
+    check(w, 10)

@@ -75,7 +75,7 @@ def test_stratified_background_2d():
 
 
 def test_stratified_background_3d_small():
-    w = inputs.polytrope_3d(20, 12, 18, xi=50.0, amp=1e-2)
+    w = inputs.polytrope_3d(20, 12, 40, xi=50.0, amp=1e-2, contrast=20.0)
     _assert_close(gpu_run(w, 5), oracle_run(w, 5), w["gamma"])
 
 
