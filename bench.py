@@ -138,7 +138,16 @@ def _max_over_ranks(x: float, world: int) -> float:
 
 def workload(args):
     from paper_1812_04135_gb300 import inputs
+    if args.workload == "polytrope3d":
+        return inputs.polytrope_3d(variant=args.variant)
     return inputs.shear_layer_2d(args.n, args.n, xi=30.0, variant=args.variant, ratio=10.0)
+
+
+def bytes_per_cell_stage(w, precision):
+    """Algorithmic HBM bytes per cell per stage: stage 1 reads and writes one
+    state, stage 2 reads two and writes one: 2.5 * nvar * bytes per scalar."""
+    nvar = w["ndim"] + 2
+    return 2.5 * nvar * (8 if precision == "fp64" else 4)
 
 
 def cpu_baseline(w, seconds: float):
@@ -187,10 +196,14 @@ def run_reference(args, world, rank):
 
 
 def _config(args, w):
-    return {"workload": f"2D periodic shear layer {w['n'][0]}x{w['n'][1]} FP64, Mach 0.01, density ratio 10, "
-                        f"xi=30, {args.variant.upper()} form, adaptive CFL 0.4",
-            "cells": int(np.prod(w["n"])), "variant": args.variant, "precision": "fp64",
-            "l2": "256 MiB buffer written between timed steps (state fits in L2)",
+    if args.workload == "polytrope3d":
+        desc = (f"3D polytropic stratified box 256x128x128 {args.precision.upper()}, contrast 100, gravity -z, "
+                f"reflecting z walls, xi=50, {args.variant.upper()} form, adaptive CFL 0.4")
+    else:
+        desc = (f"2D periodic shear layer {w['n'][0]}x{w['n'][1]} {args.precision.upper()}, Mach 0.01, "
+                f"density ratio 10, xi=30, {args.variant.upper()} form, adaptive CFL 0.4")
+    return {"workload": desc, "cells": int(np.prod(w["n"])), "variant": args.variant, "precision": args.precision,
+            "l2": "256 MiB buffer written between timed steps",
             "parallelism": f"replicas x{args.gpus}"}
 
 
@@ -201,7 +214,7 @@ def run_gpu(args, world, rank, local):
     w = workload(args)
     cells = int(np.prod(w["n"]))
     stream = torch.cuda.current_stream(dev)
-    s = rsst.Solver(w, "fp64", stream=stream)
+    s = rsst.Solver(w, args.precision, stream=stream)
     U0 = torch.from_numpy(w["U"]).to(dev)
     s.set_state(U0)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
@@ -254,19 +267,26 @@ def run_gpu(args, world, rank, local):
     c = clk.summary()
     sm_mhz = c["sm_mhz"] or peaks.get("clocks_under_load", {}).get("sm_mhz_median", 1900.0)
     launch_s = t_dev / (2 * args.steps)
-    flops = FP64_FLOPS_PER_CELL_STAGE_2D * cells
-    peak_tf = fp64_peak_tflops(sm_mhz)
-    achieved_tf = flops / launch_s / 1e12
-    alg_bytes = 40 * cells * 2          # 2.5 * nvar * 8 B per cell-stage, nvar = 4
+    alg_bytes = bytes_per_cell_stage(w, args.precision) * cells
+    hbm_gbs = alg_bytes / launch_s / 1e9
+    if args.precision == "fp64" and w["ndim"] == 2:
+        flops = FP64_FLOPS_PER_CELL_STAGE_2D * cells
+        peak_tf = fp64_peak_tflops(sm_mhz)
+        achieved_tf = flops / launch_s / 1e12
+        roof = {"bound": "alu", "achieved": achieved_tf, "peak": peak_tf, "unit": "TFLOP/s",
+                "frac": achieved_tf / peak_tf, "traffic": None,
+                "peak_source": f"float64: 152 SMs x 2 DFMA/clk x 2 flop x {sm_mhz:.0f} MHz (unit count measured)",
+                "hbm_achieved_gbs": hbm_gbs, "hbm_peak_gbs": peaks["hbm_gbs"],
+                "hbm_frac": hbm_gbs / peaks["hbm_gbs"], "hbm_peak_source": src}
+    else:
+        roof = {"bound": "hbm", "achieved": hbm_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": hbm_gbs / peaks["hbm_gbs"], "traffic": None, "peak_source": src}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_max / args.steps * 1e3, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": _config(args, w),
-            "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": peak_tf, "unit": "TFLOP/s",
-                         "frac": achieved_tf / peak_tf, "traffic": None,
-                         "peak_source": f"float64: 152 SMs x 2 DFMA/clk x 2 flop x {sm_mhz:.0f} MHz (unit count measured)",
-                         "hbm_achieved_gbs": alg_bytes / launch_s / 1e9, "hbm_peak_gbs": peaks["hbm_gbs"],
-                         "hbm_frac": alg_bytes / launch_s / 1e9 / peaks["hbm_gbs"], "hbm_peak_source": src},
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if args.precision == "fp64" else "f32 (perturbation about an f64 background)",
+            "data": "synthetic", "config": _config(args, w),
+            "roofline": roof,
             "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
             "gpu_launches": launches, "clocks": c, "wall_s": wall,
             "step_ms_min": min(step_ms), "step_ms_median": statistics.median(step_ms)}
@@ -283,6 +303,8 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--n", type=int, default=512)
     ap.add_argument("--variant", default="pvs")
+    ap.add_argument("--workload", default="shear2d", choices=["shear2d", "polytrope3d"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32_pert"])
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

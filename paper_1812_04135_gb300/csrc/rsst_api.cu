@@ -6,6 +6,8 @@
 #include <cstdlib>
 #include <cstring>
 
+#include <cudaTypedefs.h>
+
 #include "rsst_internal.h"
 
 static thread_local char g_err[512] = "";
@@ -50,11 +52,43 @@ struct rsst_handle {
   double* h_small;      // pinned host scratch for small read-backs
   float* d_tab;         // background tables (float32 mode), or null
   PhysF pf;
+  int use_tma2d;        // 2D float32 runs use the TMA-staged kernel
+  CUtensorMap tmap[2];  // tensor maps of buf[0], buf[1] (TMA kernels)
   int slot;
   int64_t launches;
 };
 
 static int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+
+// cuTensorMapEncodeTiled from the driver, looked up once (no link-time libcuda).
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* ptr = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)ptr;
+  }
+  return fn;
+}
+
+// Tiled float32 map of a padded 2D state [nvar][py][pitch], box of one tile
+// plus halo for every field (x: 4 columns each side so the origin stays on a
+// 16-byte boundary; y: 2 rows each side).
+static int make_tmap_2d(CUtensorMap* m, void* base, const Geom& g, int nv, int box_x, int box_y) {
+  auto enc = tensor_map_encoder();
+  if (!enc) { rsst_set_error("cuTensorMapEncodeTiled unavailable from the driver"); return RSST_ECUDA; }
+  const cuuint64_t dims[3] = {(cuuint64_t)g.pitch, (cuuint64_t)g.py, (cuuint64_t)nv};
+  const cuuint64_t strides[2] = {(cuuint64_t)g.pitch * 4, (cuuint64_t)g.fstride * 4};
+  const cuuint32_t box[3] = {(cuuint32_t)box_x, (cuuint32_t)box_y, (cuuint32_t)nv};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box, estr,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) { rsst_set_error("cuTensorMapEncodeTiled failed (%d)", (int)r); return RSST_ECUDA; }
+  return RSST_OK;
+}
 
 static int validate(const rsst_config* c) {
   if (!c) { rsst_set_error("config is NULL"); return RSST_EINVAL; }
@@ -206,6 +240,13 @@ extern "C" int rsst_init(rsst_handle** out, const rsst_config* cfg, void* stream
     goto fail;
   }
 #undef ALLOC
+  if (cfg->precision == RSST_FP32_PERT && cfg->ndim == 2 && (cfg->vertical == -1 || cfg->vertical == 1)) {
+    h->use_tma2d = 1;
+    for (int b = 0; b < 2; ++b) {
+      rc = make_tmap_2d(&h->tmap[b], h->buf[b], h->g, nv, 72, 36);
+      if (rc != RSST_OK) goto fail;
+    }
+  }
   *out = h;
   return RSST_OK;
 fail:
@@ -287,12 +328,14 @@ static int run_steps(rsst_handle* h, double dt, int nsteps) {
     a.base = nullptr;
     a.out = Us;
     if constexpr (sizeof(T) == 8) RC_TRY(rsst_launch_stage_fp64(a, h->stream));
+    else if (h->use_tma2d) RC_TRY(rsst_launch_stage2d_tma(&h->tmap[0], a, h->stream));
     else RC_TRY(rsst_launch_stage_fp32(a, h->stream));
     a.stage = 2;
     a.in = Us;
     a.base = U;
     a.out = U;
     if constexpr (sizeof(T) == 8) RC_TRY(rsst_launch_stage_fp64(a, h->stream));
+    else if (h->use_tma2d) RC_TRY(rsst_launch_stage2d_tma(&h->tmap[1], a, h->stream));
     else RC_TRY(rsst_launch_stage_fp32(a, h->stream));
     h->launches += 2;
     h->slot ^= 1;

@@ -1,6 +1,7 @@
 // Internal types shared by the librsst translation units (host and device).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -97,6 +98,7 @@ int rsst_launch_sums_fp64(const double* U, const Geom& g, double* partial, doubl
                           double scale, cudaStream_t s);
 
 int rsst_launch_stage_fp32(const StageArgs<float>& a, cudaStream_t s);
+int rsst_launch_stage2d_tma(const CUtensorMap* tin, const StageArgs<float>& a, cudaStream_t s);
 int rsst_launch_bgtab(const double* bg, int bg_len, const Geom& g, const Phys& p, float* tab, cudaStream_t s);
 int rsst_launch_pack_fp32(const double* src, float* dst, const Geom& g, const Phys& p, const double* bg,
                           int bg_len, cudaStream_t s);

@@ -22,11 +22,13 @@
 
 namespace rsst {
 
-// Monotonized-central slope (Sec. 4.2), float32.
+// Monotonized-central slope (Sec. 4.2), float32, branch-free: the magnitude
+// min(2|a|, 2|b|, |a+b|/2) with the sign of a, zero unless ab > 0.  Equal to
+// the branch-wise form (equal magnitudes of same-sign candidates are equal
+// values, so the tie rule does not change the result).
 __device__ __forceinline__ float mc_slope_f(float a, float b) {
-  const float aa = 2.0f * fabsf(a), bb = 2.0f * fabsf(b), cc = 0.5f * fabsf(a + b);
-  const float s = (aa <= bb && aa <= cc) ? 2.0f * a : ((bb <= cc) ? 2.0f * b : 0.5f * (a + b));
-  return (a * b > 0.0f) ? s : 0.0f;
+  const float m = fminf(2.0f * fminf(fabsf(a), fabsf(b)), 0.5f * fabsf(a + b));
+  return (a * b > 0.0f) ? copysignf(m, a) : 0.0f;
 }
 
 // Branch of the MC slope: 0 -> 0, 1 -> 2a, 2 -> 2b, 3 -> (a+b)/2.
@@ -89,6 +91,101 @@ __device__ __forceinline__ void pert_flux_f(const float (&q1)[NV], float rho0, f
 #pragma unroll
   for (int e = 0; e < ND; ++e) F[1 + e] = q1[1 + e] * v[D] + (e == D ? P1 : 0.0f);
   F[NV - 1] = (H0 + q1[NV - 1] + P1) * v[D];
+}
+
+}  // namespace rsst
+
+namespace rsst {
+
+// Perturbation slope of a component whose background varies along the axis:
+// lin_B(d1) + [lin_B(d0) - MC(d0)], B the branch of MC on d0 + d1.
+// row points at the component's six slope rows (d0L, d0R, four deltas), stride sv.
+__device__ __forceinline__ float bg_slope_f(const float* row, int sv, int r, float da, float db) {
+  const int b = mc_branch_f(row[r] + da, row[sv + r] + db);
+  return mc_linear_f(b, da, db) + row[(2 + b) * sv + r];
+}
+
+// Cell update of the float32 perturbation state (Sec. 4.2 steps 6-8):
+// L = R0 + div-part, reduced by -f s r from the full-state primitives, plus
+// the perturbation force (rho1 F, m.F); then the RK combine.  Dl is the Euler
+// tendency including the background's (for s).  Returns the new state in u,
+// and in stage 2 the CFL rate and the physical check of the new state.
+template <int NV>
+__device__ __forceinline__ void cell_update_f(const float (&q)[NV], float (&L)[NV], const float (&Dl)[NV], float rho0,
+                                              float P0, const PhysF& pf, int variant, bool has_grav, int stage,
+                                              float dt, const float* base_vals, float (&u)[NV], float& rate,
+                                              bool& ok) {
+  constexpr int ND = NV - 2;
+  const float rho = rho0 + q[0];
+  const float ir = 1.0f / rho;
+  float vel[ND];
+  float v2 = 0.0f, mv = 0.0f, vdm = 0.0f;
+#pragma unroll
+  for (int e = 0; e < ND; ++e) {
+    vel[e] = q[1 + e] * ir;
+    v2 += vel[e] * vel[e];
+    mv += q[1 + e] * vel[e];
+    vdm += vel[e] * Dl[1 + e];
+  }
+  const float P = P0 + pf.gm1 * (q[NV - 1] - 0.5f * mv);
+  if (variant != RSST_EULER) {
+    const float e_int = P * pf.inv_gm1;
+    const float kin = 0.5f * mv;
+    float s, r0, rv, rE;
+    if (variant == RSST_PVS || variant == RSST_PMS || variant == RSST_PD) {
+      s = pf.gm1 * (0.5f * v2 * Dl[0] - vdm + Dl[NV - 1]);
+      if (variant == RSST_PD) {
+        r0 = 0.0f; rv = 0.0f; rE = pf.inv_gm1;
+      } else {
+        const float ia2 = rho / (pf.gamma * P);
+        r0 = ia2;
+        rv = variant == RSST_PVS ? ia2 : 0.0f;
+        rE = (variant == RSST_PVS ? (e_int + P + kin) : (e_int + P - kin)) * ia2 * ir;
+      }
+    } else {
+      s = Dl[0];
+      r0 = 1.0f;
+      rv = variant == RSST_DVS ? 1.0f : 0.0f;
+      rE = (variant == RSST_DVS ? (e_int + P + kin) : (e_int + P - kin)) * ir;
+    }
+    const float fs = pf.f * s;
+    L[0] -= fs * r0;
+#pragma unroll
+    for (int e = 0; e < ND; ++e) L[1 + e] -= fs * (rv * vel[e]);
+    L[NV - 1] -= fs * rE;
+  }
+  if (has_grav) {
+    float mg = 0.0f;
+#pragma unroll
+    for (int e = 0; e < ND; ++e) {
+      L[1 + e] += q[0] * pf.grav[e];
+      mg += q[1 + e] * pf.grav[e];
+    }
+    L[NV - 1] += mg;
+  }
+  rate = 0.0f;
+  ok = true;
+  if (stage == 1) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) u[v] = q[v] + dt * L[v];
+  } else {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) u[v] = 0.5f * base_vals[v] + 0.5f * (q[v] + dt * L[v]);
+    const float rn = rho0 + u[0];
+    const float irn = 1.0f / rn;
+    float w2 = 0.0f, mw = 0.0f;
+    bool fin = isfinite(u[0]) && isfinite(u[NV - 1]);
+#pragma unroll
+    for (int e = 0; e < ND; ++e) {
+      const float ve = u[1 + e] * irn;
+      w2 += ve * ve;
+      mw += u[1 + e] * ve;
+      fin = fin && isfinite(u[1 + e]);
+    }
+    const float Pn = P0 + pf.gm1 * (u[NV - 1] - 0.5f * mw);
+    ok = fin && rn > 0.0f && Pn > 0.0f;
+    if (ok) rate = (sqrtf(w2) + sqrtf(pf.gamma * Pn * irn) * pf.inv_xi) * pf.sum_inv_dx;
+  }
 }
 
 }  // namespace rsst

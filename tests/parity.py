@@ -64,5 +64,6 @@ def rel_linf_pert(got, ref, w):
     out = []
     for k in range(ref.shape[0]):
         den = float((ref[k] - U0[k]).abs().max())
-        out.append(float((got[k] - ref[k]).abs().max()) / den if den > 0 else float("inf"))
+        num = float((got[k] - ref[k]).abs().max())
+        out.append(num / den if den > 0 else (0.0 if num == 0.0 else float("inf")))
     return out
