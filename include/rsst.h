@@ -132,6 +132,27 @@ int rsst_sync(rsst_handle* h);
  * Synchronous. */
 int rsst_conserved_sums(rsst_handle* h, double* sums);
 
+/* Conservation sums of a caller-held state, for callers that cannot allocate
+ * device memory when they need them (inside stream capture, where cudaMalloc
+ * is not allowed; inside another framework that owns the device-memory
+ * budget; in loops that cannot take cudaMalloc's device synchronisation).
+ * The paper has no counterpart: it is a deployment convenience.
+ *   U     device pointer, float64, caller layout [nvar][nz][ny][nx], read only
+ *   ndim  1..3 (nvar = ndim + 2 <= 5); n, dx: host arrays of ndim entries
+ *   sums  device pointer to nvar doubles, written with sum(U) * cell volume
+ *   stream cudaStream_t (may be NULL); the call is asynchronous.
+ * Allocates nothing: its only scratch is a file-scope device array of
+ * 5 x 1024 doubles (40 KiB) that every GPU loading the library keeps until
+ * exit.  The first call on a device looks that array's address up
+ * (cudaGetSymbolAddress) with the device current, so make the first call on
+ * each device before any stream capture.  Calls share the array: two calls
+ * that overlap on the GPU (different streams, not ordered) race and give wrong
+ * sums.  Each call overwrites every scratch entry it reads, so no clearing is
+ * needed.  Rejects ndim outside 1..3 and grids above 2^31 cells with
+ * RSST_EINVAL.  Same reduction order as rsst_conserved_sums. */
+int rsst_conserved_sums_noalloc(const double* U, int32_t ndim, const int32_t* n, const double* dx, double* sums,
+                                void* stream);
+
 /* Number of kernels the library launched through this handle so far. */
 int64_t rsst_kernel_launches(const rsst_handle* h);
 

@@ -60,6 +60,7 @@ def lib():
             "rsst_sync": (i32, [vp]),
             "rsst_conserved_sums": (i32, [vp, pd]),
             "rsst_kernel_launches": (i64, [vp]),
+            "rsst_conserved_sums_noalloc": (i32, [vp, i32, C.POINTER(C.c_int32), pd, vp, vp]),
             "rsst_config_size": (C.c_size_t, []),
             "rsst_last_error": (C.c_char_p, []),
         }
@@ -160,6 +161,16 @@ def rsst_conserved_sums(h: int, nvar: int) -> list:
     out = (C.c_double * nvar)()
     _check(lib().rsst_conserved_sums(h, out), "rsst_conserved_sums")
     return list(out)
+
+
+def rsst_conserved_sums_noalloc(U, n, dx, sums, stream=None) -> None:
+    """Conservation sums without allocation: U (float64 CUDA tensor, caller
+    layout) and sums (float64 CUDA tensor of nvar entries) belong to the caller."""
+    ndim = len(n)
+    nn = (C.c_int32 * ndim)(*[int(v) for v in n])
+    dd = (C.c_double * ndim)(*[float(v) for v in dx])
+    _check(lib().rsst_conserved_sums_noalloc(U.data_ptr(), ndim, nn, dd, sums.data_ptr(), _stream_ptr(stream)),
+           "rsst_conserved_sums_noalloc")
 
 
 def rsst_kernel_launches(h: int) -> int:
