@@ -132,6 +132,48 @@ int rsst_sync(rsst_handle* h);
  * Synchronous. */
 int rsst_conserved_sums(rsst_handle* h, double* sums);
 
+/* ---- Batched runs (one persistent kernel per RK stage for all runs) ------
+ * Many independent 2D RSST_FP32_PERT runs (vertical axis y or none) of
+ * uneven size, xi and background, advanced together (the method of Sec. 4.2
+ * per run; batching is this library's, the paper runs one problem at a
+ * time).  Each run keeps its own state, background tables and CFL dt, all on
+ * the device.  The stream must be a created stream (the two stage launches
+ * of a step are captured into a CUDA graph on it). */
+typedef struct rsst_batch rsst_batch;
+
+/* Create nruns runs from cfgs[0..nruns-1] (each as for rsst_init).  Returns
+ * RSST_EUNSUPPORTED for a run that is not 2D float32-perturbation with a y or
+ * no vertical axis.  Synchronous. */
+int rsst_batch_init(rsst_batch** b, int32_t nruns, const rsst_config* cfgs, void* stream);
+void rsst_batch_destroy(rsst_batch* b);
+
+/* Per-run state transfer, as rsst_set_state / rsst_get_state. */
+int rsst_batch_set_state(rsst_batch* b, int32_t run, const double* U, int on_host);
+int rsst_batch_get_state(rsst_batch* b, int32_t run, double* U, int on_host);
+
+/* Advance every run nsteps adaptive SSP-RK2 steps (each with its own CFL dt):
+ * per step one graph with two persistent launches over the ragged tile list
+ * of all runs.  Asynchronous. */
+int rsst_batch_step(rsst_batch* b, int nsteps);
+
+/* The same steps with one pair of single-run launches per run per step
+ * (the reference the persistent kernel is measured against). */
+int rsst_batch_step_looped(rsst_batch* b, int nsteps);
+
+/* Each run's next dt (nruns host doubles); wait and report flags.  Synchronous. */
+int rsst_batch_dt(rsst_batch* b, double* dts);
+int rsst_batch_sync(rsst_batch* b);
+
+/* Time `steps` batch steps for each of four tile shapes (64x32, 32x32, 64x16,
+ * 128x16 cells) on the current states (saved and restored around the
+ * trials), keep the fastest; *choice_out gets its index and *ms_out the
+ * milliseconds per step (either may be NULL).  With RSST_TUNE_CACHE set to a
+ * file name the choice is read from / appended to that file, keyed by the
+ * run list.  Synchronous. */
+int rsst_batch_autotune(rsst_batch* b, int steps, int32_t* choice_out, double* ms_out);
+int rsst_batch_tile_shape(const rsst_batch* b, int32_t* bx, int32_t* by);
+int64_t rsst_batch_kernel_launches(const rsst_batch* b);
+
 /* Conservation sums of a caller-held state, for callers that cannot allocate
  * device memory when they need them (inside stream capture, where cudaMalloc
  * is not allowed; inside another framework that owns the device-memory

@@ -36,27 +36,7 @@ extern "C" const char* rsst_last_error(void) { return g_err; }
     if (rc_ != RSST_OK) return rc_; \
   } while (0)
 
-struct rsst_handle {
-  rsst_config cfg;
-  Geom g;
-  Phys p;
-  cudaStream_t stream;
-  size_t elem;          // bytes per stored scalar
-  void* buf[2];         // padded state: buf[0] = U^n, buf[1] = U*
-  double* d_bg;         // [2][bg_len] rho0, E0 (float64), or null
-  int bg_len;
-  double* d_scal;       // [0..1] CFL slots, [2] dt, [8..15] sums
-  unsigned int* d_flag;
-  double* d_partial;    // sums partials
-  double* d_stage;      // caller-layout staging for host transfers
-  double* h_small;      // pinned host scratch for small read-backs
-  float* d_tab;         // background tables (float32 mode), or null
-  PhysF pf;
-  int use_tma2d;        // 2D float32 runs use the TMA-staged kernel
-  CUtensorMap tmap[2];  // tensor maps of buf[0], buf[1] (TMA kernels)
-  int slot;
-  int64_t launches;
-};
+
 
 static int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 
@@ -343,12 +323,16 @@ static int run_steps(rsst_handle* h, double dt, int nsteps) {
   return RSST_OK;
 }
 
+int rsst_handle_steps(rsst_handle* h, double dt, int nsteps) {
+  if (h->cfg.precision == RSST_FP32_PERT) return run_steps<float>(h, dt, nsteps);
+  return run_steps<double>(h, dt, nsteps);
+}
+
 extern "C" int rsst_step(rsst_handle* h, double dt, int nsteps) {
   if (!h) { rsst_set_error("NULL handle"); return RSST_EINVAL; }
   if (nsteps < 0) { rsst_set_error("nsteps must be >= 0"); return RSST_EINVAL; }
   if (!std::isfinite(dt)) { rsst_set_error("dt must be finite"); return RSST_EINVAL; }
-  if (h->cfg.precision == RSST_FP32_PERT) return run_steps<float>(h, dt, nsteps);
-  return run_steps<double>(h, dt, nsteps);
+  return rsst_handle_steps(h, dt, nsteps);
 }
 
 extern "C" int rsst_dt(rsst_handle* h, double* dt_out) {

@@ -1,0 +1,476 @@
+// Batched float32-perturbation RSST steps: many independent 2D runs of uneven
+// size, xi and background in one persistent kernel per RK stage.
+//
+// The tiles of all runs form one ragged list (prefix sums of each run's tile
+// count).  A grid of (SMs x resident CTAs) walks that list with a fixed
+// stride; each tile looks up its run (binary search), copies the run's
+// descriptor into shared memory and runs the same TMA-staged tile routine as
+// the single-run kernel with that run's tensor map, tables, dt and CFL slot.
+// The two stages of one step are captured once per CFL-slot parity into a
+// CUDA graph and replayed.  The tile shape is chosen by a timing autotuner
+// over four candidates (optionally cached in the file named by
+// RSST_TUNE_CACHE).
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include <cudaTypedefs.h>
+
+#include "rsst_fp32_2d.cuh"
+
+namespace rsst {
+
+struct BatchRun {
+  CUtensorMap tmap[2];  // maps of buf[0] and buf[1] for the chosen tile shape
+  TileRun r;            // base / out filled per stage by the kernel
+  float* buf[2];
+  double* scal;
+  int tiles_x;
+  int vert;
+};
+
+template <class C>
+__global__ void __launch_bounds__(C::NT) batch_stage_kernel(const BatchRun* __restrict__ runs,
+                                                             const int* __restrict__ tile_begin, int nruns,
+                                                             int total_tiles, int stage, int slot) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  uint64_t* bar = t2_barrier<C>(smem_raw);
+  float* sdt = reinterpret_cast<float*>(bar + 1);
+  int* srun = reinterpret_cast<int*>(bar + 1) + 1;
+  TileRun* sr = reinterpret_cast<TileRun*>(t2_extra<C>(smem_raw));
+  static_assert(sizeof(TileRun) <= 512, "run descriptor must fit the reserved shared memory");
+  if (threadIdx.x == 0) {
+    mbar_init(bar, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  uint32_t phase = 0;
+  for (int t = blockIdx.x; t < total_tiles; t += gridDim.x) {
+    if (threadIdx.x == 0) {
+      int lo = 0, hi = nruns - 1;  // last run with tile_begin <= t
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (tile_begin[mid] <= t) lo = mid; else hi = mid - 1;
+      }
+      *srun = lo;
+      const BatchRun& br = runs[lo];
+      *sr = br.r;
+      sr->base = stage == 2 ? br.buf[0] : nullptr;
+      sr->out = stage == 2 ? br.buf[0] : br.buf[1];
+      sr->stage = stage;
+      const double dtd = br.r.p.cfl / br.scal[slot];
+      *sdt = (float)dtd;
+      if (stage == 1 && t == tile_begin[lo]) {
+        br.scal[slot ^ 1] = 0.0;
+        br.scal[2] = dtd;
+      }
+    }
+    __syncthreads();
+    const int run = *srun;
+    const BatchRun& br = runs[run];
+    const int local = t - tile_begin[run];
+    const int tx = local % br.tiles_x, ty = local / br.tiles_x;
+    const CUtensorMap* map = &br.tmap[stage == 1 ? 0 : 1];
+    float rmax = 0.0f;
+    bool ok = true;
+    const bool fine = br.vert == 1 ? tile2d_f<C, 1>(map, *sr, *sdt, tx, ty, smem_raw, phase, rmax, ok)
+                                   : tile2d_f<C, -1>(map, *sr, *sdt, tx, ty, smem_raw, phase, rmax, ok);
+    if (!fine) return;
+    if (stage == 2) {
+      if (!ok) atomicOr(sr->flag, 1u);
+      block_max_to<C::NT>((double)rmax, br.scal + (slot ^ 1), t2_sred<C>(smem_raw));
+    }
+    __syncthreads();  // the descriptor copy is rewritten for the next tile
+  }
+}
+
+// Candidate tile shapes for the autotuner.
+using TC0 = T2Cfg<64, 32, 8>;
+using TC1 = T2Cfg<32, 32, 8>;
+using TC2 = T2Cfg<64, 16, 4>;
+using TC3 = T2Cfg<128, 16, 8>;
+constexpr int NCAND = 4;
+static const int CAND_BX[NCAND] = {64, 32, 64, 128};
+static const int CAND_BY[NCAND] = {32, 32, 16, 16};
+
+}  // namespace rsst
+
+using namespace rsst;
+
+struct rsst_batch {
+  int nruns;
+  cudaStream_t stream;
+  std::vector<rsst_handle*> runs;
+  BatchRun* d_runs;
+  int* d_tile_begin;
+  int choice;
+  int total_tiles;
+  int grid;
+  int slot;
+  bool graph_ok[2];
+  cudaGraphExec_t graph[2];
+  int64_t launches;
+};
+
+static PFN_cuTensorMapEncodeTiled_v12000 batch_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* ptr = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)ptr;
+  }
+  return fn;
+}
+
+template <class C>
+static void* kernel_of() {
+  return (void*)batch_stage_kernel<C>;
+}
+
+static void* cand_kernel(int c, int* nt, size_t* smem) {
+  switch (c) {
+    case 0: *nt = TC0::NT; *smem = TC0::smem_bytes(); return kernel_of<TC0>();
+    case 1: *nt = TC1::NT; *smem = TC1::smem_bytes(); return kernel_of<TC1>();
+    case 2: *nt = TC2::NT; *smem = TC2::smem_bytes(); return kernel_of<TC2>();
+    default: *nt = TC3::NT; *smem = TC3::smem_bytes(); return kernel_of<TC3>();
+  }
+}
+
+static void destroy_graphs(rsst_batch* b) {
+  for (int p = 0; p < 2; ++p) {
+    if (b->graph_ok[p]) cudaGraphExecDestroy(b->graph[p]);
+    b->graph_ok[p] = false;
+  }
+}
+
+// Build the device descriptors (tensor maps, tile list) for candidate c.
+static int build_descriptors(rsst_batch* b, int c) {
+  auto enc = batch_encoder();
+  if (!enc) { rsst_set_error("cuTensorMapEncodeTiled unavailable from the driver"); return RSST_ECUDA; }
+  const int bx = CAND_BX[c], by = CAND_BY[c];
+  std::vector<BatchRun> host(b->nruns);
+  std::vector<int> begin(b->nruns + 1);
+  int total = 0;
+  for (int i = 0; i < b->nruns; ++i) {
+    rsst_handle* h = b->runs[i];
+    BatchRun& br = host[i];
+    memset(&br, 0, sizeof br);
+    for (int k = 0; k < 2; ++k) {
+      const cuuint64_t dims[3] = {(cuuint64_t)h->g.pitch, (cuuint64_t)h->g.py, 4};
+      const cuuint64_t strides[2] = {(cuuint64_t)h->g.pitch * 4, (cuuint64_t)h->g.fstride * 4};
+      const cuuint32_t box[3] = {(cuuint32_t)(bx + 8), (cuuint32_t)(by + 4), 4};
+      const cuuint32_t estr[3] = {1, 1, 1};
+      const CUresult r = enc(&br.tmap[k], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, h->buf[k], dims, strides, box, estr,
+                             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                             CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+      if (r != CUDA_SUCCESS) { rsst_set_error("cuTensorMapEncodeTiled failed (%d) for run %d", (int)r, i); return RSST_ECUDA; }
+      br.buf[k] = (float*)h->buf[k];
+    }
+    br.r.g = h->g;
+    br.r.p = h->p;
+    br.r.pf = h->pf;
+    br.r.tab = h->d_tab;
+    br.r.tab_len = h->bg_len;
+    br.r.flag = h->d_flag;
+    br.scal = h->d_scal;
+    br.tiles_x = (h->g.n[0] + bx - 1) / bx;
+    br.vert = h->d_tab ? 1 : -1;
+    begin[i] = total;
+    total += br.tiles_x * ((h->g.n[1] + by - 1) / by);
+  }
+  begin[b->nruns] = total;
+  if (cudaMemcpy(b->d_runs, host.data(), sizeof(BatchRun) * b->nruns, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(b->d_tile_begin, begin.data(), sizeof(int) * (b->nruns + 1), cudaMemcpyHostToDevice) != cudaSuccess) {
+    rsst_set_error("batch descriptor upload failed");
+    return RSST_ECUDA;
+  }
+  int nt;
+  size_t smem;
+  void* k = cand_kernel(c, &nt, &smem);
+  if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+    rsst_set_error("cudaFuncSetAttribute failed for the batch kernel");
+    return RSST_ECUDA;
+  }
+  int per_sm = 0, dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, nt, smem) != cudaSuccess || per_sm < 1) per_sm = 1;
+  b->grid = sms * per_sm < total ? sms * per_sm : total;
+  if (b->grid < 1) b->grid = 1;
+  b->total_tiles = total;
+  b->choice = c;
+  destroy_graphs(b);
+  return RSST_OK;
+}
+
+static int launch_stage(rsst_batch* b, int stage, int slot) {
+  int nt;
+  size_t smem;
+  cand_kernel(b->choice, &nt, &smem);
+  switch (b->choice) {
+    case 0: batch_stage_kernel<TC0><<<b->grid, nt, smem, b->stream>>>(b->d_runs, b->d_tile_begin, b->nruns, b->total_tiles, stage, slot); break;
+    case 1: batch_stage_kernel<TC1><<<b->grid, nt, smem, b->stream>>>(b->d_runs, b->d_tile_begin, b->nruns, b->total_tiles, stage, slot); break;
+    case 2: batch_stage_kernel<TC2><<<b->grid, nt, smem, b->stream>>>(b->d_runs, b->d_tile_begin, b->nruns, b->total_tiles, stage, slot); break;
+    default: batch_stage_kernel<TC3><<<b->grid, nt, smem, b->stream>>>(b->d_runs, b->d_tile_begin, b->nruns, b->total_tiles, stage, slot); break;
+  }
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    rsst_set_error("batch stage launch: %s", cudaGetErrorString(e));
+    return RSST_ECUDA;
+  }
+  return RSST_OK;
+}
+
+static int capture_graphs(rsst_batch* b) {
+  for (int p = 0; p < 2; ++p) {
+    if (b->graph_ok[p]) continue;
+    cudaGraph_t g = nullptr;
+    if (cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      rsst_set_error("cudaStreamBeginCapture failed (the batch stream must be a created stream)");
+      return RSST_ECUDA;
+    }
+    int rc = launch_stage(b, 1, p);
+    if (rc == RSST_OK) rc = launch_stage(b, 2, p);
+    const cudaError_t e = cudaStreamEndCapture(b->stream, &g);
+    if (rc != RSST_OK) return rc;
+    if (e != cudaSuccess || cudaGraphInstantiate(&b->graph[p], g, 0) != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      rsst_set_error("graph capture of the batch step failed");
+      return RSST_ECUDA;
+    }
+    cudaGraphDestroy(g);
+    b->graph_ok[p] = true;
+  }
+  return RSST_OK;
+}
+
+extern "C" void rsst_batch_destroy(rsst_batch* b) {
+  if (!b) return;
+  destroy_graphs(b);
+  for (rsst_handle* h : b->runs) rsst_destroy(h);
+  cudaFree(b->d_runs);
+  cudaFree(b->d_tile_begin);
+  delete b;
+}
+
+extern "C" int rsst_batch_init(rsst_batch** out, int32_t nruns, const rsst_config* cfgs, void* stream) {
+  if (!out || !cfgs || nruns < 1) { rsst_set_error("rsst_batch_init: bad arguments"); return RSST_EINVAL; }
+  *out = nullptr;
+  for (int i = 0; i < nruns; ++i) {
+    const rsst_config& c = cfgs[i];
+    if (c.ndim != 2 || c.precision != RSST_FP32_PERT || !(c.vertical == -1 || c.vertical == 1)) {
+      rsst_set_error("rsst_batch_init: run %d must be 2D, RSST_FP32_PERT, vertical axis y or none", i);
+      return RSST_EUNSUPPORTED;
+    }
+  }
+  rsst_batch* b = new rsst_batch();
+  b->nruns = nruns;
+  b->stream = (cudaStream_t)stream;
+  b->d_runs = nullptr;
+  b->d_tile_begin = nullptr;
+  b->slot = 0;
+  b->launches = 0;
+  b->graph_ok[0] = b->graph_ok[1] = false;
+  for (int i = 0; i < nruns; ++i) {
+    rsst_handle* h = nullptr;
+    const int rc = rsst_init(&h, &cfgs[i], stream);
+    if (rc != RSST_OK) {
+      rsst_batch_destroy(b);
+      return rc;
+    }
+    b->runs.push_back(h);
+  }
+  if (cudaMalloc((void**)&b->d_runs, sizeof(BatchRun) * nruns) != cudaSuccess ||
+      cudaMalloc((void**)&b->d_tile_begin, sizeof(int) * (nruns + 1)) != cudaSuccess) {
+    cudaGetLastError();
+    rsst_set_error("rsst_batch_init: descriptor allocation failed");
+    rsst_batch_destroy(b);
+    return RSST_ENOMEM;
+  }
+  const int rc = build_descriptors(b, 0);
+  if (rc != RSST_OK) {
+    rsst_batch_destroy(b);
+    return rc;
+  }
+  *out = b;
+  return RSST_OK;
+}
+
+extern "C" int rsst_batch_set_state(rsst_batch* b, int32_t run, const double* U, int on_host) {
+  if (!b || run < 0 || run >= b->nruns) { rsst_set_error("rsst_batch_set_state: bad run index"); return RSST_EINVAL; }
+  b->runs[run]->slot = b->slot;
+  return rsst_set_state(b->runs[run], U, on_host);
+}
+
+extern "C" int rsst_batch_get_state(rsst_batch* b, int32_t run, double* U, int on_host) {
+  if (!b || run < 0 || run >= b->nruns) { rsst_set_error("rsst_batch_get_state: bad run index"); return RSST_EINVAL; }
+  return rsst_get_state(b->runs[run], U, on_host);
+}
+
+static void sync_slots(rsst_batch* b) {
+  for (rsst_handle* h : b->runs) h->slot = b->slot;
+}
+
+extern "C" int rsst_batch_step(rsst_batch* b, int nsteps) {
+  if (!b || nsteps < 0) { rsst_set_error("rsst_batch_step: bad arguments"); return RSST_EINVAL; }
+  if (nsteps == 0) return RSST_OK;
+  const int rc = capture_graphs(b);
+  if (rc != RSST_OK) return rc;
+  for (int s = 0; s < nsteps; ++s) {
+    const cudaError_t e = cudaGraphLaunch(b->graph[b->slot], b->stream);
+    if (e != cudaSuccess) {
+      rsst_set_error("batch graph launch: %s", cudaGetErrorString(e));
+      return RSST_ECUDA;
+    }
+    b->slot ^= 1;
+    b->launches += 2;
+  }
+  sync_slots(b);
+  return RSST_OK;
+}
+
+extern "C" int rsst_batch_step_looped(rsst_batch* b, int nsteps) {
+  if (!b || nsteps < 0) { rsst_set_error("rsst_batch_step_looped: bad arguments"); return RSST_EINVAL; }
+  for (int s = 0; s < nsteps; ++s) {
+    for (rsst_handle* h : b->runs) {
+      h->slot = b->slot;
+      const int rc = rsst_handle_steps(h, 0.0, 1);
+      if (rc != RSST_OK) return rc;
+      b->launches += 2;
+    }
+    b->slot ^= 1;
+  }
+  sync_slots(b);
+  return RSST_OK;
+}
+
+extern "C" int rsst_batch_dt(rsst_batch* b, double* dts) {
+  if (!b || !dts) { rsst_set_error("rsst_batch_dt: NULL argument"); return RSST_EINVAL; }
+  for (int i = 0; i < b->nruns; ++i) {
+    const int rc = rsst_dt(b->runs[i], &dts[i]);
+    if (rc != RSST_OK) return rc;
+  }
+  return RSST_OK;
+}
+
+extern "C" int rsst_batch_sync(rsst_batch* b) {
+  if (!b) { rsst_set_error("NULL batch"); return RSST_EINVAL; }
+  for (rsst_handle* h : b->runs) {
+    const int rc = rsst_sync(h);
+    if (rc != RSST_OK) return rc;
+  }
+  return RSST_OK;
+}
+
+extern "C" int rsst_batch_tile_shape(const rsst_batch* b, int32_t* bx, int32_t* by) {
+  if (!b || !bx || !by) { rsst_set_error("NULL argument"); return RSST_EINVAL; }
+  *bx = CAND_BX[b->choice];
+  *by = CAND_BY[b->choice];
+  return RSST_OK;
+}
+
+extern "C" int64_t rsst_batch_kernel_launches(const rsst_batch* b) { return b ? b->launches : 0; }
+
+static std::string batch_signature(const rsst_batch* b) {
+  std::string s = "n" + std::to_string(b->nruns);
+  for (rsst_handle* h : b->runs)
+    s += ":" + std::to_string(h->g.n[0]) + "x" + std::to_string(h->g.n[1]) + (h->d_tab ? "b" : "p");
+  unsigned long long hsh = 1469598103934665603ull;  // FNV-1a of the run list
+  for (char c : s) hsh = (hsh ^ (unsigned char)c) * 1099511628211ull;
+  char buf[32];
+  snprintf(buf, sizeof buf, "%016llx", hsh);
+  return buf;
+}
+
+extern "C" int rsst_batch_autotune(rsst_batch* b, int steps, int32_t* choice_out, double* ms_out) {
+  if (!b || steps < 1) { rsst_set_error("rsst_batch_autotune: bad arguments"); return RSST_EINVAL; }
+  const std::string sig = batch_signature(b);
+  const char* cache = getenv("RSST_TUNE_CACHE");
+  if (cache) {
+    FILE* f = fopen(cache, "r");
+    if (f) {
+      char key[64];
+      int c;
+      while (fscanf(f, "%63s %d", key, &c) == 2) {
+        if (sig == key && c >= 0 && c < NCAND) {
+          fclose(f);
+          const int rc = build_descriptors(b, c);
+          if (choice_out) *choice_out = c;
+          return rc;
+        }
+      }
+      fclose(f);
+    }
+  }
+  // save every run's state and scalars, time each candidate, restore
+  std::vector<void*> save(b->nruns, nullptr);
+  std::vector<double*> ssave(b->nruns, nullptr);
+  int rc = RSST_OK;
+  for (int i = 0; i < b->nruns && rc == RSST_OK; ++i) {
+    rsst_handle* h = b->runs[i];
+    const size_t bytes = (size_t)(h->g.ndim + 2) * h->g.fstride * h->elem;
+    if (cudaMalloc(&save[i], bytes) != cudaSuccess || cudaMalloc((void**)&ssave[i], 16 * sizeof(double)) != cudaSuccess) {
+      cudaGetLastError();
+      rsst_set_error("rsst_batch_autotune: backup allocation failed");
+      rc = RSST_ENOMEM;
+      break;
+    }
+    cudaMemcpyAsync(save[i], h->buf[0], bytes, cudaMemcpyDeviceToDevice, b->stream);
+    cudaMemcpyAsync(ssave[i], h->d_scal, 16 * sizeof(double), cudaMemcpyDeviceToDevice, b->stream);
+  }
+  const int slot0 = b->slot;
+  double best_ms = 1e30;
+  int best = 0;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  for (int c = 0; c < NCAND && rc == RSST_OK; ++c) {
+    rc = build_descriptors(b, c);
+    if (rc != RSST_OK) break;
+    b->slot = slot0;
+    rc = rsst_batch_step(b, 1);  // warm-up (and graph capture)
+    if (rc != RSST_OK) break;
+    cudaEventRecord(e0, b->stream);
+    rc = rsst_batch_step(b, steps);
+    cudaEventRecord(e1, b->stream);
+    cudaEventSynchronize(e1);
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = c;
+    }
+    for (int i = 0; i < b->nruns; ++i) {  // restore
+      rsst_handle* h = b->runs[i];
+      const size_t bytes = (size_t)(h->g.ndim + 2) * h->g.fstride * h->elem;
+      cudaMemcpyAsync(h->buf[0], save[i], bytes, cudaMemcpyDeviceToDevice, b->stream);
+      cudaMemcpyAsync(h->d_scal, ssave[i], 16 * sizeof(double), cudaMemcpyDeviceToDevice, b->stream);
+    }
+  }
+  cudaStreamSynchronize(b->stream);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  for (int i = 0; i < b->nruns; ++i) {
+    cudaFree(save[i]);
+    cudaFree(ssave[i]);
+  }
+  b->slot = slot0;
+  sync_slots(b);
+  if (rc != RSST_OK) return rc;
+  rc = build_descriptors(b, best);
+  if (rc != RSST_OK) return rc;
+  if (choice_out) *choice_out = best;
+  if (ms_out) *ms_out = best_ms / steps;
+  if (cache) {
+    FILE* f = fopen(cache, "a");
+    if (f) {
+      fprintf(f, "%s %d\n", sig.c_str(), best);
+      fclose(f);
+    }
+  }
+  return RSST_OK;
+}

@@ -33,7 +33,7 @@ __global__ void __launch_bounds__(T2::NT, 2) stage2d_tma_kernel(const __grid_con
   r.tab_len = a.tab_len;
   r.flag = a.flag;
   r.stage = a.stage;
-  uint64_t* bar = t2_barrier(smem_raw);
+  uint64_t* bar = t2_barrier<T2>(smem_raw);
   float* sdt = reinterpret_cast<float*>(bar + 1);
   if (threadIdx.x == 0) {
     // the float64 division is done once per CTA, not per thread
@@ -51,11 +51,11 @@ __global__ void __launch_bounds__(T2::NT, 2) stage2d_tma_kernel(const __grid_con
   uint32_t phase = 0;
   float rmax = 0.0f;
   bool ok = true;
-  const bool fine = tile2d_f<VERT>(&tin, r, dtf, blockIdx.x, blockIdx.y, smem_raw, phase, rmax, ok);
+  const bool fine = tile2d_f<T2, VERT>(&tin, r, dtf, blockIdx.x, blockIdx.y, smem_raw, phase, rmax, ok);
   if (!fine) return;
   if (a.stage == 2) {
     if (!ok) atomicOr(a.flag, 1u);
-    block_max_to<T2::NT>((double)rmax, a.scal + (a.slot ^ 1), t2_sred(smem_raw));
+    block_max_to<T2::NT>((double)rmax, a.scal + (a.slot ^ 1), t2_sred<T2>(smem_raw));
   }
 }
 
@@ -66,7 +66,7 @@ using namespace rsst;
 int rsst_launch_stage2d_tma(const CUtensorMap* tin, const StageArgs<float>& a, cudaStream_t s) {
   const int vert = a.tab ? a.p.vertical : -1;
   dim3 grid((a.g.n[0] + T2::BX - 1) / T2::BX, (a.g.n[1] + T2::BY - 1) / T2::BY, 1);
-  const size_t smem = T2::smem_bytes(vert >= 0);
+  const size_t smem = T2::smem_bytes();
   if (vert == 1) {
     static bool attr = false;
     if (!attr) {

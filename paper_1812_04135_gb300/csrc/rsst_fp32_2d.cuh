@@ -8,28 +8,41 @@
 
 namespace rsst {
 
-// Tile geometry: 64 x 32 cells, 256 threads, each owning one column of 8.
-struct T2 {
-  static constexpr int NV = 4, BX = 64, BY = 32, NT = 256;
+// Tile geometry: BX_ x BY_ cells, each thread owning one column of SEG_
+// cells (BX_ * BY_ / SEG_ threads).  Shared memory: the TMA box (halo tile,
+// all fields), the x fluxes, the background rows, a barrier, dt, reduction.
+template <int BX_, int BY_, int SEG_>
+struct T2Cfg {
+  static constexpr int NV = 4, BX = BX_, BY = BY_, SEG = SEG_;
+  static constexpr int NT = BX * (BY / SEG);
   static constexpr int SXP = BX + 8;   // TMA box width: 4 columns each side (2 used), 16-byte aligned origin
   static constexpr int SYP = BY + 4;   // halo rows
   static constexpr int XO = 4;         // smem column of tile x = 0
   static constexpr int FXW = BX + 1;   // x faces per row
-  static constexpr int SEG = 8;        // cells per thread in the column march
   static constexpr int U_FLOATS = NV * SYP * SXP;
   static constexpr int FX_FLOATS = NV * BY * FXW;
   static constexpr int TAB_FLOATS = TB_COUNT * SYP;
+  static constexpr size_t SCRATCH = (size_t)(U_FLOATS + FX_FLOATS + TAB_FLOATS) * 4;
   static constexpr uint32_t BOX_BYTES = U_FLOATS * 4;
-  static constexpr size_t smem_bytes(bool) {
-    return (size_t)(U_FLOATS + FX_FLOATS + TAB_FLOATS) * 4 + 16 + 8 * 8 + 128;
-  }
+  static constexpr size_t smem_bytes() { return SCRATCH + 16 + 8 * 8 + 512 + 128; }
+  static_assert(BY % SEG == 0, "column segments must tile BY");
+  static_assert(SXP <= 256 && SYP <= 256, "TMA box dimensions are at most 256");
 };
 
+using T2 = T2Cfg<64, 32, 8>;  // single-run default
+
+template <class C>
 __device__ __forceinline__ uint64_t* t2_barrier(unsigned char* smem) {
-  return reinterpret_cast<uint64_t*>(smem + (size_t)(T2::U_FLOATS + T2::FX_FLOATS + T2::TAB_FLOATS) * 4);
+  return reinterpret_cast<uint64_t*>(smem + C::SCRATCH);
 }
+template <class C>
 __device__ __forceinline__ double* t2_sred(unsigned char* smem) {
-  return reinterpret_cast<double*>(smem + (size_t)(T2::U_FLOATS + T2::FX_FLOATS + T2::TAB_FLOATS) * 4 + 16);
+  return reinterpret_cast<double*>(smem + C::SCRATCH + 16);
+}
+// free shared memory after the reduction slots (used by the batched kernel)
+template <class C>
+__device__ __forceinline__ unsigned char* t2_extra(unsigned char* smem) {
+  return smem + C::SCRATCH + 16 + 8 * 8;
 }
 
 // Everything one tile needs about its run.
@@ -46,7 +59,7 @@ struct TileRun {
 };
 
 // LLF flux of the x face between tile cells with smem columns c-1 | c (row sr).
-template <int VERT>
+template <class T2, int VERT>
 __device__ __forceinline__ void t2_xflux(const float* __restrict__ sU, const float* __restrict__ st, int sr, int c,
                                          const PhysF& pf, float (&F)[4]) {
   constexpr int NV = 4;
@@ -73,7 +86,7 @@ __device__ __forceinline__ void t2_xflux(const float* __restrict__ sU, const flo
 }
 
 // MC slope along y of the cell at smem row r from its neighbours' values.
-template <int VERT>
+template <class T2, int VERT>
 __device__ __forceinline__ void t2_yslope(const float (&um)[4], const float (&u0)[4], const float (&up)[4],
                                           const float* __restrict__ st, int r, float (&s)[4]) {
 #pragma unroll
@@ -87,7 +100,7 @@ __device__ __forceinline__ void t2_yslope(const float (&um)[4], const float (&u0
 }
 
 // y-face flux between cells (u0, s0) below and (u1, s1) above; face table at smem row rf.
-template <int VERT>
+template <class T2, int VERT>
 __device__ __forceinline__ void t2_yflux(const float (&u0)[4], const float (&s0)[4], const float (&u1)[4],
                                          const float (&s1)[4], const float* __restrict__ st, int rf, const PhysF& pf,
                                          float (&F)[4]) {
@@ -126,14 +139,14 @@ __device__ __forceinline__ void t2_yflux(const float (&u0)[4], const float (&s0)
 // Process tile (tx, ty) of run r: returns false if the TMA wait timed out
 // (flag set).  Accumulates the stage-2 CFL rate maximum and physical check.
 // The caller initialised the barrier; `phase` is its current parity.
-template <int VERT>
+template <class T2, int VERT>
 __device__ __forceinline__ bool tile2d_f(const CUtensorMap* tin, const TileRun& r, float dt, int tx, int ty,
                                          unsigned char* smem, uint32_t& phase, float& rmax, bool& ok_all) {
   constexpr int NV = 4;
   float* sU = reinterpret_cast<float*>(smem);
   float* sFx = sU + T2::U_FLOATS;
   float* st = sFx + T2::FX_FLOATS;
-  uint64_t* bar = t2_barrier(smem);
+  uint64_t* bar = t2_barrier<T2>(smem);
   const Geom& g = r.g;
   const PhysF& pf = r.pf;
   const int i0 = tx * T2::BX, j0 = ty * T2::BY;
@@ -167,14 +180,14 @@ __device__ __forceinline__ bool tile2d_f(const CUtensorMap* tin, const TileRun& 
     const int fx = fid - row * T2::FXW;
     if (i0 + fx > nx || j0 + row >= ny) continue;
     float F[NV];
-    t2_xflux<VERT>(sU, st, row + 2, fx + T2::XO, pf, F);
+    t2_xflux<T2, VERT>(sU, st, row + 2, fx + T2::XO, pf, F);
 #pragma unroll
     for (int v = 0; v < NV; ++v) sFx[(v * T2::BY + row) * T2::FXW + fx] = F[v];
   }
   __syncthreads();
 
   // column march with the fused epilogue
-  const int col = tid & (T2::BX - 1);
+  const int col = tid % T2::BX;
   const int seg = tid / T2::BX;
   const int x = i0 + col;
   const int jb = seg * T2::SEG;  // first tile row of this thread
@@ -190,9 +203,9 @@ __device__ __forceinline__ bool tile2d_f(const CUtensorMap* tin, const TileRun& 
     ld(jb + 1, um);
     ld(jb + 2, u0);
     ld(jb + 3, u1);
-    t2_yslope<VERT>(u2, um, u0, st, jb + 1, sm);   // slope of cell jb-1
-    t2_yslope<VERT>(um, u0, u1, st, jb + 2, s0);   // slope of cell jb
-    t2_yflux<VERT>(um, sm, u0, s0, st, jb + 2, pf, Fm);
+    t2_yslope<T2, VERT>(u2, um, u0, st, jb + 1, sm);   // slope of cell jb-1
+    t2_yslope<T2, VERT>(um, u0, u1, st, jb + 2, s0);   // slope of cell jb
+    t2_yflux<T2, VERT>(um, sm, u0, s0, st, jb + 2, pf, Fm);
     const float idx = pf.inv_dx[0], idy = pf.inv_dx[1];
     const int64_t fs = g.fstride;
 #pragma unroll 1
@@ -200,8 +213,8 @@ __device__ __forceinline__ bool tile2d_f(const CUtensorMap* tin, const TileRun& 
       const int j = jb + jj;       // tile row of the cell
       if (j0 + j >= ny) break;
       ld(j + 4, u2);               // cell j+2
-      t2_yslope<VERT>(u0, u1, u2, st, j + 3, s1);   // slope of cell j+1
-      t2_yflux<VERT>(u0, s0, u1, s1, st, j + 3, pf, Fp);
+      t2_yslope<T2, VERT>(u0, u1, u2, st, j + 3, s1);   // slope of cell j+1
+      t2_yflux<T2, VERT>(u0, s0, u1, s1, st, j + 3, pf, Fp);
       float L[4], Dl[4];
 #pragma unroll
       for (int v = 0; v < NV; ++v) {

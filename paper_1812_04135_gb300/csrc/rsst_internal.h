@@ -110,3 +110,29 @@ int rsst_launch_sums_fp32(const float* U, const Geom& g, const Phys& p, const do
                           double* partial, double* out, double scale, cudaStream_t s);
 
 void rsst_set_error(const char* fmt, ...);
+
+// One run: configuration, padded state buffers, background, scalars.
+struct rsst_handle {
+  rsst_config cfg;
+  Geom g;
+  Phys p;
+  cudaStream_t stream;
+  size_t elem;          // bytes per stored scalar
+  void* buf[2];         // padded state: buf[0] = U^n, buf[1] = U*
+  double* d_bg;         // [2][bg_len] rho0, E0 (float64), or null
+  int bg_len;
+  double* d_scal;       // [0..1] CFL slots, [2] dt, [8..15] sums
+  unsigned int* d_flag;
+  double* d_partial;    // sums partials
+  double* d_stage;      // caller-layout staging for host transfers
+  double* h_small;      // pinned host scratch for small read-backs
+  float* d_tab;         // background tables (float32 mode), or null
+  PhysF pf;
+  int use_tma2d;        // 2D float32 runs use the TMA-staged kernel
+  CUtensorMap tmap[2];  // tensor maps of buf[0], buf[1] (TMA kernels)
+  int slot;
+  int64_t launches;
+};
+
+// Step a single run (used by rsst_step and by the batch's looped mode).
+int rsst_handle_steps(rsst_handle* h, double dt, int nsteps);

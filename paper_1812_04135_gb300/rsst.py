@@ -62,6 +62,17 @@ def lib():
             "rsst_kernel_launches": (i64, [vp]),
             "rsst_conserved_sums_noalloc": (i32, [vp, i32, C.POINTER(C.c_int32), pd, vp, vp]),
             "rsst_config_size": (C.c_size_t, []),
+            "rsst_batch_init": (i32, [C.POINTER(vp), i32, C.POINTER(Config), vp]),
+            "rsst_batch_destroy": (None, [vp]),
+            "rsst_batch_set_state": (i32, [vp, i32, vp, i32]),
+            "rsst_batch_get_state": (i32, [vp, i32, vp, i32]),
+            "rsst_batch_step": (i32, [vp, i32]),
+            "rsst_batch_step_looped": (i32, [vp, i32]),
+            "rsst_batch_dt": (i32, [vp, pd]),
+            "rsst_batch_sync": (i32, [vp]),
+            "rsst_batch_autotune": (i32, [vp, i32, C.POINTER(C.c_int32), pd]),
+            "rsst_batch_tile_shape": (i32, [vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
+            "rsst_batch_kernel_launches": (i64, [vp]),
             "rsst_last_error": (C.c_char_p, []),
         }
         for name, (res, args) in sig.items():
@@ -224,6 +235,124 @@ class Solver:
         if getattr(self, "h", None):
             rsst_destroy(self.h)
             self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# --- batched runs -----------------------------------------------------------
+
+def rsst_batch_init(cfgs, stream) -> int:
+    arr = (Config * len(cfgs))(*cfgs)
+    h = C.c_void_p()
+    _check(lib().rsst_batch_init(C.byref(h), len(cfgs), arr, _stream_ptr(stream)), "rsst_batch_init")
+    return h.value
+
+
+def rsst_batch_destroy(b: int) -> None:
+    lib().rsst_batch_destroy(b)
+
+
+def rsst_batch_set_state(b: int, run: int, U, on_host: bool = False) -> None:
+    ptr = U.ctypes.data if isinstance(U, np.ndarray) else U.data_ptr()
+    _check(lib().rsst_batch_set_state(b, run, ptr, int(on_host)), "rsst_batch_set_state")
+
+
+def rsst_batch_get_state(b: int, run: int, U, on_host: bool = False) -> None:
+    ptr = U.ctypes.data if isinstance(U, np.ndarray) else U.data_ptr()
+    _check(lib().rsst_batch_get_state(b, run, ptr, int(on_host)), "rsst_batch_get_state")
+
+
+def rsst_batch_step(b: int, nsteps: int = 1) -> None:
+    _check(lib().rsst_batch_step(b, int(nsteps)), "rsst_batch_step")
+
+
+def rsst_batch_step_looped(b: int, nsteps: int = 1) -> None:
+    _check(lib().rsst_batch_step_looped(b, int(nsteps)), "rsst_batch_step_looped")
+
+
+def rsst_batch_dt(b: int, nruns: int) -> list:
+    out = (C.c_double * nruns)()
+    _check(lib().rsst_batch_dt(b, out), "rsst_batch_dt")
+    return list(out)
+
+
+def rsst_batch_sync(b: int) -> None:
+    _check(lib().rsst_batch_sync(b), "rsst_batch_sync")
+
+
+def rsst_batch_autotune(b: int, steps: int = 3):
+    c = C.c_int32()
+    ms = C.c_double()
+    _check(lib().rsst_batch_autotune(b, int(steps), C.byref(c), C.byref(ms)), "rsst_batch_autotune")
+    return c.value, ms.value
+
+
+def rsst_batch_tile_shape(b: int):
+    bx, by = C.c_int32(), C.c_int32()
+    _check(lib().rsst_batch_tile_shape(b, C.byref(bx), C.byref(by)), "rsst_batch_tile_shape")
+    return bx.value, by.value
+
+
+def rsst_batch_kernel_launches(b: int) -> int:
+    return int(lib().rsst_batch_kernel_launches(b))
+
+
+class BatchSolver:
+    """Many 2D float32-perturbation runs on one device, on a stream of their own."""
+
+    def __init__(self, workloads, stream=None):
+        import torch
+        self.ws = list(workloads)
+        self.cfgs = [config_from_workload(w, precision="fp32_pert") for w in self.ws]
+        self.stream = stream if stream is not None else torch.cuda.Stream()
+        self.b = rsst_batch_init(self.cfgs, self.stream)
+        self.nruns = len(self.ws)
+
+    def set_state(self, run: int, U) -> None:
+        import torch
+        if isinstance(U, np.ndarray):
+            U = torch.from_numpy(np.ascontiguousarray(U, dtype=np.float64))
+        U = U.contiguous()
+        self._keep = getattr(self, "_keep", {})
+        self._keep[run] = U
+        rsst_batch_set_state(self.b, run, U, on_host=not U.is_cuda)
+
+    def get_state(self, run: int, device="cuda"):
+        import torch
+        w = self.ws[run]
+        out = torch.empty((w["ndim"] + 2,) + tuple(reversed(w["n"])), dtype=torch.float64, device=device)
+        rsst_batch_get_state(self.b, run, out, on_host=(out.device.type == "cpu"))
+        return out
+
+    def step(self, nsteps: int = 1) -> None:
+        rsst_batch_step(self.b, nsteps)
+
+    def step_looped(self, nsteps: int = 1) -> None:
+        rsst_batch_step_looped(self.b, nsteps)
+
+    def autotune(self, steps: int = 3):
+        return rsst_batch_autotune(self.b, steps)
+
+    def tile_shape(self):
+        return rsst_batch_tile_shape(self.b)
+
+    def dts(self) -> list:
+        return rsst_batch_dt(self.b, self.nruns)
+
+    def sync(self) -> None:
+        rsst_batch_sync(self.b)
+
+    def launches(self) -> int:
+        return rsst_batch_kernel_launches(self.b)
+
+    def close(self) -> None:
+        if getattr(self, "b", None):
+            rsst_batch_destroy(self.b)
+            self.b = None
 
     def __del__(self):
         try:
