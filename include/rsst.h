@@ -132,6 +132,35 @@ int rsst_sync(rsst_handle* h);
  * Synchronous. */
 int rsst_conserved_sums(rsst_handle* h, double* sums);
 
+/* ---- Discrete adjoint (float64 runs) ----------------------------------------
+ * Reverse mode of the discrete SSP-RK2 step (transpose of the Jacobian of
+ * U^n -> U^{n+1}; the paper gives the forward method only).  dt is held
+ * fixed; non-smooth operations take the branch of the forward pass (MC
+ * branch, LLF max with ties to the left state, zero subgradient of |V| at
+ * V = 0).  Gradients are with respect to every component of the initial
+ * conserved state and to xi. */
+
+/* Run nsteps fixed-dt steps from the current state, storing a checkpoint of
+ * the state every `every` steps (library-owned device memory).  The handle
+ * ends at U^{nsteps}.  RSST_EUNSUPPORTED for float32 runs.  Asynchronous. */
+int rsst_adjoint_record(rsst_handle* h, double dt, int nsteps, int every);
+
+/* Number of recorded segments, ceil(nsteps / every). */
+int rsst_adjoint_segments(rsst_handle* h, int32_t* nseg);
+
+/* Reverse segment `seg` (call from the last segment down to 0): recompute its
+ * steps from the checkpoint, then apply the step adjoints in reverse.  lam:
+ * device pointer, caller layout, float64; on entry dJ/dU at the segment's end,
+ * on return dJ/dU at its start.  *dJ_dxi (host) is incremented by the
+ * segment's contribution.  The handle's current state is preserved.
+ * Synchronous. */
+int rsst_adjoint_step(rsst_handle* h, int32_t seg, double* lam, double* dJ_dxi);
+
+/* J = sum_cells |m|^2/(2 rho) * cell volume of the current state (host
+ * double) and, if grad is not NULL, dJ/dU into grad (device, caller layout:
+ * (-|V|^2/2, V, 0) * cell volume).  Float64 runs.  Synchronous. */
+int rsst_kinetic_energy(rsst_handle* h, double* J, double* grad);
+
 /* ---- Batched runs (one persistent kernel per RK stage for all runs) ------
  * Many independent 2D RSST_FP32_PERT runs (vertical axis y or none) of
  * uneven size, xi and background, advanced together (the method of Sec. 4.2

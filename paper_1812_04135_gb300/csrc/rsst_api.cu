@@ -144,6 +144,7 @@ static void make_phys(const rsst_config* c, Phys* p) {
 
 extern "C" void rsst_destroy(rsst_handle* h) {
   if (!h) return;
+  rsst_adjoint_free(h);
   cudaFree(h->buf[0]);
   cudaFree(h->buf[1]);
   cudaFree(h->d_bg);

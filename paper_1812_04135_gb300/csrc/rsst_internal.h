@@ -130,9 +130,12 @@ struct rsst_handle {
   PhysF pf;
   int use_tma2d;        // 2D float32 runs use the TMA-staged kernel
   CUtensorMap tmap[2];  // tensor maps of buf[0], buf[1] (TMA kernels)
+  void* adj;            // adjoint checkpoints and work arrays, or null
   int slot;
   int64_t launches;
 };
+
+void rsst_adjoint_free(rsst_handle* h);
 
 // Step a single run (used by rsst_step and by the batch's looped mode).
 int rsst_handle_steps(rsst_handle* h, double dt, int nsteps);

@@ -62,6 +62,10 @@ def lib():
             "rsst_kernel_launches": (i64, [vp]),
             "rsst_conserved_sums_noalloc": (i32, [vp, i32, C.POINTER(C.c_int32), pd, vp, vp]),
             "rsst_config_size": (C.c_size_t, []),
+            "rsst_adjoint_record": (i32, [vp, dbl, i32, i32]),
+            "rsst_adjoint_segments": (i32, [vp, C.POINTER(C.c_int32)]),
+            "rsst_adjoint_step": (i32, [vp, i32, vp, pd]),
+            "rsst_kinetic_energy": (i32, [vp, pd, vp]),
             "rsst_batch_init": (i32, [C.POINTER(vp), i32, C.POINTER(Config), vp]),
             "rsst_batch_destroy": (None, [vp]),
             "rsst_batch_set_state": (i32, [vp, i32, vp, i32]),
@@ -182,6 +186,29 @@ def rsst_conserved_sums_noalloc(U, n, dx, sums, stream=None) -> None:
     dd = (C.c_double * ndim)(*[float(v) for v in dx])
     _check(lib().rsst_conserved_sums_noalloc(U.data_ptr(), ndim, nn, dd, sums.data_ptr(), _stream_ptr(stream)),
            "rsst_conserved_sums_noalloc")
+
+
+def rsst_adjoint_record(h: int, dt: float, nsteps: int, every: int) -> None:
+    _check(lib().rsst_adjoint_record(h, float(dt), int(nsteps), int(every)), "rsst_adjoint_record")
+
+
+def rsst_adjoint_segments(h: int) -> int:
+    n = C.c_int32()
+    _check(lib().rsst_adjoint_segments(h, C.byref(n)), "rsst_adjoint_segments")
+    return n.value
+
+
+def rsst_adjoint_step(h: int, seg: int, lam) -> float:
+    """Reverse one segment in place on ``lam`` (float64 CUDA tensor, caller layout); returns dJ/dxi of it."""
+    acc = C.c_double(0.0)
+    _check(lib().rsst_adjoint_step(h, int(seg), lam.data_ptr(), C.byref(acc)), "rsst_adjoint_step")
+    return acc.value
+
+
+def rsst_kinetic_energy(h: int, grad=None) -> float:
+    J = C.c_double()
+    _check(lib().rsst_kinetic_energy(h, C.byref(J), None if grad is None else grad.data_ptr()), "rsst_kinetic_energy")
+    return J.value
 
 
 def rsst_kernel_launches(h: int) -> int:
@@ -359,3 +386,48 @@ class BatchSolver:
             self.close()
         except Exception:
             pass
+
+
+# --- autograd ---------------------------------------------------------------
+
+def _make_rsst_run():
+    import torch
+
+    class RsstRun(torch.autograd.Function):
+        """U_N = step^N(U_0; xi) with the library's discrete adjoint as backward.
+
+        forward(U0, xi, solver, dt, nsteps, every): the solver (a float64
+        Solver whose xi equals ``xi``) records checkpoints every ``every``
+        steps; backward reverses the segments (recompute + step adjoints) and
+        returns dJ/dU0 and dJ/dxi.  dt is held fixed."""
+
+        @staticmethod
+        def forward(ctx, U0, xi, solver, dt, nsteps, every):
+            if abs(float(xi) - solver.w["xi"]) > 0:
+                raise ValueError("xi must equal the solver's xi (the kernel reads it from the handle)")
+            solver.set_state(U0.detach().to(torch.float64).contiguous())
+            rsst_adjoint_record(solver.h, dt, nsteps, every)
+            ctx.solver = solver
+            return solver.get_state(U0.device if U0.is_cuda else "cuda").to(U0.device)
+
+        @staticmethod
+        def backward(ctx, gN):
+            s = ctx.solver
+            lam = gN.detach().to(device="cuda", dtype=torch.float64).contiguous().clone()
+            dxi = 0.0
+            for seg in reversed(range(rsst_adjoint_segments(s.h))):
+                dxi += rsst_adjoint_step(s.h, seg, lam)
+            return lam.to(gN.device), torch.tensor(dxi, dtype=torch.float64, device=gN.device), None, None, None, None
+
+    return RsstRun
+
+
+_RSST_RUN = None
+
+
+def rsst_run(U0, xi, solver, dt, nsteps, every):
+    """Differentiable run of nsteps fixed-dt steps (see RsstRun)."""
+    global _RSST_RUN
+    if _RSST_RUN is None:
+        _RSST_RUN = _make_rsst_run()
+    return _RSST_RUN.apply(U0, xi, solver, dt, nsteps, every)
