@@ -8,6 +8,20 @@
 
 namespace rsst {
 
+// 1/x to full float64 accuracy with few float64-pipe instructions: the
+// hardware reciprocal approximation followed by two Newton-Raphson steps
+// y <- y + y (1 - x y) (each doubles the number of correct bits).  Within an
+// ulp of the correctly rounded quotient for the normal, positive densities
+// it is used on.
+__device__ __forceinline__ double rcp_nr(double x) {
+  double y;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+  double e = fma(-x, y, 1.0);
+  y = fma(y, e, y);
+  e = fma(-x, y, 1.0);
+  return fma(y, e, y);
+}
+
 // Euler flux along dimension D and the approximate RSST characteristic
 // speed c_tot = |V| + a/xi of one state (Eq. pvs_dt0; Sec. 4.2).
 template <int NV, int D>
@@ -15,7 +29,7 @@ __device__ __forceinline__ void euler_flux(const double (&q)[NV], const Phys& p,
                                            double (&F)[NV], double& c) {
   constexpr int ND = NV - 2;
   const double rho = q[0];
-  const double ir = 1.0 / rho;
+  const double ir = rcp_nr(rho);
   double v[ND];
   double v2 = 0.0;
 #pragma unroll
@@ -47,10 +61,21 @@ __device__ __forceinline__ void llf_flux(const double (&qL)[NV], const double (&
 
 // Monotonized-central limited slope (named in Sec. 4.2): 0 if ab <= 0, else
 // the smallest in magnitude of 2a, 2b, (a+b)/2, ties in that order.
+// The magnitude comparisons run on the integer pipe: non-negative doubles
+// order like their bit patterns, and 2|a| <= |a+b|/2 is |a| <= |a+b|/4
+// (scaling by powers of two is exact), so only a + b, its quarter and the
+// final doubling use the float64 pipe.  Same decisions and values as the
+// direct form (for nonzero same-sign a, b; products below the smallest
+// normal double aside).
 __device__ __forceinline__ double mc_slope(double a, double b) {
-  const double aa = 2.0 * fabs(a), bb = 2.0 * fabs(b), cc = 0.5 * fabs(a + b);
-  const double s = (aa <= bb && aa <= cc) ? 2.0 * a : ((bb <= cc) ? 2.0 * b : 0.5 * (a + b));
-  return (a * b > 0.0) ? s : 0.0;
+  const long long ia = __double_as_longlong(a), ib = __double_as_longlong(b);
+  const long long mask = 0x7fffffffffffffffll;
+  const long long ma = ia & mask, mb = ib & mask;
+  const bool same = ((ia ^ ib) >= 0) && ma != 0 && mb != 0;
+  const double q = 0.25 * (a + b);
+  const long long mq = __double_as_longlong(q) & mask;
+  const double pick = (ma <= mb && ma <= mq) ? a : ((mb <= mq) ? b : q);
+  return same ? 2.0 * pick : 0.0;
 }
 
 // Reduced tendency: dU <- dU - (1 - 1/xi^2) s r, then the external force.
@@ -67,7 +92,7 @@ __device__ __forceinline__ void rsst_rhs(const double (&q)[NV], double (&dU)[NV]
   constexpr int ND = NV - 2;
   const double rho = q[0];
   if (p.variant != RSST_EULER) {
-    const double ir = 1.0 / rho;
+    const double ir = rcp_nr(rho);
     double v[ND];
     double v2 = 0.0, vdm = 0.0;
 #pragma unroll
@@ -86,7 +111,7 @@ __device__ __forceinline__ void rsst_rhs(const double (&q)[NV], double (&dU)[NV]
       if (var == RSST_PD) {
         r0 = 0.0; rv = 0.0; rE = p.inv_gm1;
       } else {
-        const double ia2 = rho / (p.gamma * P);  // 1/a^2
+        const double ia2 = rho * rcp_nr(p.gamma * P);  // 1/a^2
         r0 = ia2;
         rv = (var == RSST_PVS) ? ia2 : 0.0;
         rE = (var == RSST_PVS ? (e_int + P + kin) : (e_int + P - kin)) * ia2 * ir;
@@ -119,7 +144,7 @@ template <int NV>
 __device__ __forceinline__ double cfl_rate(const double (&q)[NV], const Phys& p, bool& ok) {
   constexpr int ND = NV - 2;
   const double rho = q[0];
-  const double ir = 1.0 / rho;
+  const double ir = rcp_nr(rho);
   double v2 = 0.0;
   bool fin = isfinite(q[0]) && isfinite(q[NV - 1]);
 #pragma unroll

@@ -186,3 +186,10 @@ def test_host_buffers_roundtrip():
     got = s.get_state("cpu")
     assert torch.equal(got, torch.from_numpy(w["U"]))
     s.close()
+
+
+def test_float64_helpers_against_cuda():
+    """Newton-Raphson reciprocal within 1 ulp of CUDA's 1.0/x; integer-pipe
+    MC limiter identical to the direct float64 form."""
+    ulp, bad = rsst.rsst_math_selftest(1 << 20)
+    assert ulp <= 1.0 and bad == 0, (ulp, bad)
