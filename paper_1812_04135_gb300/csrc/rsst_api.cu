@@ -125,6 +125,7 @@ static void make_phys(const rsst_config* c, Phys* p) {
   p->gamma = c->gamma;
   p->gm1 = c->gamma - 1.0;
   p->inv_gm1 = 1.0 / (c->gamma - 1.0);
+  p->hgm1 = 0.5 * (c->gamma - 1.0);
   p->xi = c->xi;
   p->inv_xi = 1.0 / c->xi;
   p->f = 1.0 - 1.0 / (c->xi * c->xi);

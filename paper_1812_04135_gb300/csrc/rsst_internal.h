@@ -28,7 +28,7 @@ struct Geom {
 
 // Physics and scheme constants, precomputed on the host.
 struct Phys {
-  double gamma, gm1, inv_gm1;
+  double gamma, gm1, inv_gm1, hgm1;  // hgm1 = (gamma - 1)/2
   double xi, inv_xi, f;  // f = 1 - 1/xi^2
   double cfl;
   double grav[3];

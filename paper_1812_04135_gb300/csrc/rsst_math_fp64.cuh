@@ -22,8 +22,8 @@ __device__ __forceinline__ double rcp_nr(double x) {
   return fma(y, e, y);
 }
 
-// Euler flux along dimension D and the approximate RSST characteristic
-// speed c_tot = |V| + a/xi of one state (Eq. pvs_dt0; Sec. 4.2).
+// Half the Euler flux along dimension D, F/2, and the approximate RSST
+// characteristic speed c_tot = |V| + a/xi of one state (Eq. pvs_dt0; Sec. 4.2).
 template <int NV, int D>
 __device__ __forceinline__ void euler_flux(const double (&q)[NV], const Phys& p,
                                            double (&F)[NV], double& c) {
@@ -37,13 +37,15 @@ __device__ __forceinline__ void euler_flux(const double (&q)[NV], const Phys& p,
     v[e] = q[1 + e] * ir;
     v2 += v[e] * v[e];
   }
-  const double P = p.gm1 * (q[NV - 1] - 0.5 * rho * v2);
+  const double P = p.gm1 * q[NV - 1] - p.hgm1 * (rho * v2);
   const double a = sqrt(p.gamma * P * ir);
   c = sqrt(v2) + a * p.inv_xi;
-  F[0] = q[1 + D];
+  // half fluxes: the LLF average of the two sides needs F/2
+  const double hv = 0.5 * v[D];
+  F[0] = 0.5 * q[1 + D];
 #pragma unroll
-  for (int e = 0; e < ND; ++e) F[1 + e] = q[1 + e] * v[D] + (e == D ? P : 0.0);
-  F[NV - 1] = (q[NV - 1] + P) * v[D];
+  for (int e = 0; e < ND; ++e) F[1 + e] = (e == D) ? fma(q[1 + e], hv, 0.5 * P) : q[1 + e] * hv;
+  F[NV - 1] = (q[NV - 1] + P) * hv;
 }
 
 // Local Lax-Friedrichs flux with alpha = max(c_tot(qL), c_tot(qR)), ties to
@@ -51,31 +53,32 @@ __device__ __forceinline__ void euler_flux(const double (&q)[NV], const Phys& p,
 template <int NV, int D>
 __device__ __forceinline__ void llf_flux(const double (&qL)[NV], const double (&qR)[NV],
                                          const Phys& p, double (&F)[NV]) {
-  double FL[NV], FR[NV], cL, cR;
+  double FL[NV], FR[NV], cL, cR;  // half fluxes
   euler_flux<NV, D>(qL, p, FL, cL);
   euler_flux<NV, D>(qR, p, FR, cR);
-  const double alpha = (cL >= cR) ? cL : cR;
+  const double halpha = 0.5 * ((cL >= cR) ? cL : cR);
 #pragma unroll
-  for (int k = 0; k < NV; ++k) F[k] = 0.5 * (FL[k] + FR[k]) - 0.5 * alpha * (qR[k] - qL[k]);
+  for (int k = 0; k < NV; ++k) F[k] = fma(-halpha, qR[k] - qL[k], FL[k] + FR[k]);
 }
 
 // Monotonized-central limited slope (named in Sec. 4.2): 0 if ab <= 0, else
 // the smallest in magnitude of 2a, 2b, (a+b)/2, ties in that order.
-// The magnitude comparisons run on the integer pipe: non-negative doubles
-// order like their bit patterns, and 2|a| <= |a+b|/2 is |a| <= |a+b|/4
-// (scaling by powers of two is exact), so only a + b, its quarter and the
-// final doubling use the float64 pipe.  Same decisions and values as the
-// direct form (for nonzero same-sign a, b; products below the smallest
-// normal double aside).
+// Only a + b uses the float64 pipe.  Non-negative doubles order like their
+// bit patterns, so the magnitude comparisons run on the integer pipe, and
+// scaling a normal double by 2, 4 or 1/2 is an exact change of its exponent
+// field (2|a| <= |a+b|/2 is |a| * 4 <= |a+b|).  Same decisions and values
+// as the direct form for normal operands; differences of physical states
+// are exactly zero or far above the subnormal range.
 __device__ __forceinline__ double mc_slope(double a, double b) {
-  const long long ia = __double_as_longlong(a), ib = __double_as_longlong(b);
+  const long long one = 1ll << 52;  // +1 in the exponent field
   const long long mask = 0x7fffffffffffffffll;
+  const long long ia = __double_as_longlong(a), ib = __double_as_longlong(b);
   const long long ma = ia & mask, mb = ib & mask;
   const bool same = ((ia ^ ib) >= 0) && ma != 0 && mb != 0;
-  const double q = 0.25 * (a + b);
-  const long long mq = __double_as_longlong(q) & mask;
-  const double pick = (ma <= mb && ma <= mq) ? a : ((mb <= mq) ? b : q);
-  return same ? 2.0 * pick : 0.0;
+  const long long is = __double_as_longlong(a + b);
+  const long long ms = is & mask;
+  const long long pick = (ma <= mb && ma + 2 * one <= ms) ? ia + one : ((mb + 2 * one <= ms) ? ib + one : is - one);
+  return same ? __longlong_as_double(pick) : 0.0;
 }
 
 // Reduced tendency: dU <- dU - (1 - 1/xi^2) s r, then the external force.
