@@ -42,6 +42,30 @@ L2_FLUSH_BYTES = 256 << 20
 FP64_FLOPS_PER_CELL_STAGE_2D = 2 * (122 + 6) + 8 + 45
 
 
+def _sources_sha(files):
+    import hashlib
+    h = hashlib.sha1()
+    for f in files:
+        with open(os.path.join(ROOT, "paper_1812_04135_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def _traffic_for(args, w):
+    """DRAM bytes per launch of the dominant kernel from the committed ncu
+    summary (profiles/traffic.json), only if its sources are unchanged."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        table = json.load(f)
+    key = f"{args.workload}:{args.precision}:{w['n'][0]}"
+    e = table.get(key)
+    if not e or _sources_sha(e["sources"]) != e["sources_sha"]:
+        return None
+    return e["dram_bytes_per_launch"]
+
+
 def _peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -117,7 +141,8 @@ def _dist():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if world > 1:
         import torch.distributed as dist
-        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+        backend = os.environ.get("RSST_DIST_BACKEND") or ("nccl" if torch.cuda.is_available() else "gloo")
+        dist.init_process_group(backend)
     return world, rank, local
 
 
@@ -131,7 +156,8 @@ def _max_over_ranks(x: float, world: int) -> float:
     if world == 1:
         return x
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    on_gpu = dist.get_backend() == "nccl"
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if on_gpu else "cpu")
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 
@@ -148,6 +174,83 @@ def bytes_per_cell_stage(w, precision):
     state, stage 2 reads two and writes one: 2.5 * nvar * bytes per scalar."""
     nvar = w["ndim"] + 2
     return 2.5 * nvar * (8 if precision == "fp64" else 4)
+
+
+def _time_single(w, precision, steps, warmup, dev, flush_l2):
+    """Device time of `steps` single-run SSP-RK2 steps (events per step)."""
+    from paper_1812_04135_gb300 import rsst
+    stream = torch.cuda.current_stream(dev)
+    s = rsst.Solver(w, precision, stream=stream)
+    s.set_state(torch.from_numpy(w["U"]).to(dev))
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev) if flush_l2 else None
+    for _ in range(warmup):
+        s.step(1)
+    s.sync()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    torch.cuda.synchronize()
+    for k in range(steps):
+        if flush is not None:
+            flush.fill_(float(k))
+        ev[k][0].record(stream)
+        s.step(1)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    s.sync()
+    s.close()
+    return sum(a.elapsed_time(b) for a, b in ev) / 1e3
+
+
+def _mode_line(w, precision, t, steps, peaks, extra=None):
+    cells = int(np.prod(w["n"]))
+    launch_s = t / (2 * steps)
+    gbs = bytes_per_cell_stage(w, precision) * cells / launch_s / 1e9
+    d = {"value": cells * 2 * steps / t, "unit": UNIT, "ms_per_step": t / steps * 1e3, "cells": cells,
+         "hbm_achieved_gbs": gbs, "hbm_frac": gbs / peaks["hbm_gbs"]}
+    if extra:
+        d.update(extra)
+    return d
+
+
+def run_modes(dev, peaks, sm_mhz):
+    """The other measured configurations, briefly, for the same JSON line."""
+    from paper_1812_04135_gb300 import inputs, rsst
+    out = {}
+    w = inputs.shear_layer_2d(512, 512, xi=30.0, variant="pvs")
+    out["fp32_pert_shear_512"] = _mode_line(w, "fp32_pert", _time_single(w, "fp32_pert", 20, 3, dev, True), 20, peaks,
+                                            {"bound": "hbm (instruction-issue limited)"})
+    w = inputs.shear_layer_2d(2048, 2048, xi=30.0, variant="pvs")
+    out["fp32_pert_shear_2048"] = _mode_line(w, "fp32_pert", _time_single(w, "fp32_pert", 20, 3, dev, False), 20, peaks,
+                                             {"bound": "hbm (instruction-issue limited)"})
+    w = inputs.polytrope_3d(variant="pvs")
+    t = _time_single(w, "fp64", 5, 2, dev, False)
+    out["fp64_polytrope_3d"] = _mode_line(w, "fp64", t, 5, peaks, {"bound": "alu (float64)"})
+    out["fp32_pert_polytrope_3d"] = _mode_line(w, "fp32_pert", _time_single(w, "fp32_pert", 20, 3, dev, False), 20,
+                                               peaks, {"bound": "hbm (instruction-issue limited)"})
+    # adjoint: 2D 256^2 stratified box, 400 steps, checkpoint every 20
+    w = inputs.polytrope_2d(256, 256, xi=20.0, contrast=20.0, amp=1e-3)
+    s = rsst.Solver(w, "fp64", stream=torch.cuda.current_stream(dev))
+    s.set_state(torch.from_numpy(w["U"]).to(dev))
+    dt = s.dt()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    rsst.rsst_adjoint_record(s.h, dt, 400, 20)
+    torch.cuda.synchronize()
+    t_fwd = time.perf_counter() - t0
+    gN = torch.empty((4, 256, 256), dtype=torch.float64, device=dev)
+    rsst.rsst_kinetic_energy(s.h, gN)
+    t0 = time.perf_counter()
+    dxi = 0.0
+    for seg in reversed(range(rsst.rsst_adjoint_segments(s.h))):
+        dxi += rsst.rsst_adjoint_step(s.h, seg, gN)
+    torch.cuda.synchronize()
+    t_rev = time.perf_counter() - t0
+    s.close()
+    cells = 256 * 256
+    out["adjoint_fp64_polytrope_256"] = {
+        "value": cells * 2 * 400 / (t_fwd + t_rev), "unit": UNIT + " (forward record + reverse sweep)",
+        "forward_s": t_fwd, "reverse_s": t_rev, "reverse_over_forward": t_rev / t_fwd,
+        "steps": 400, "checkpoint_every": 20, "dJ_dxi": dxi}
+    return out
 
 
 def run_batched(args, world, rank, local):
@@ -367,6 +470,11 @@ def run_gpu(args, world, rank, local):
             "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
             "gpu_launches": launches, "clocks": c, "wall_s": wall,
             "step_ms_min": min(step_ms), "step_ms_median": statistics.median(step_ms)}
+    trf = _traffic_for(args, w)
+    if trf is not None:
+        line["roofline"]["traffic"] = trf
+    if world == 1 and not args.no_modes and args.workload == "shear2d" and args.precision == "fp64" and args.n == 512:
+        line["modes"] = run_modes(dev, peaks, sm_mhz)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w, args.cpu_seconds)
     print(json.dumps(line), flush=True)
@@ -384,6 +492,7 @@ def main():
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32_pert"])
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-modes", action="store_true", help="only the headline configuration")
     args = ap.parse_args()
     world, rank, local = _dist()
     if args.impl == "reference":
