@@ -56,6 +56,22 @@ static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 // Tiled float32 map of a padded 2D state [nvar][py][pitch], box of one tile
 // plus halo for every field (x: 4 columns each side so the origin stays on a
 // 16-byte boundary; y: 2 rows each side).
+// Tiled float32 map of a padded 3D state [nvar][pz][py][pitch]: one z-plane
+// of a tile with its x/y halo for every field.
+static int make_tmap_3d(CUtensorMap* m, void* base, const Geom& g, int nv, int box_x, int box_y) {
+  auto enc = tensor_map_encoder();
+  if (!enc) { rsst_set_error("cuTensorMapEncodeTiled unavailable from the driver"); return RSST_ECUDA; }
+  const cuuint64_t dims[4] = {(cuuint64_t)g.pitch, (cuuint64_t)g.py, (cuuint64_t)g.pz, (cuuint64_t)nv};
+  const cuuint64_t strides[3] = {(cuuint64_t)g.pitch * 4, (cuuint64_t)g.plane * 4, (cuuint64_t)g.fstride * 4};
+  const cuuint32_t box[4] = {(cuuint32_t)box_x, (cuuint32_t)box_y, 1, (cuuint32_t)nv};
+  const cuuint32_t estr[4] = {1, 1, 1, 1};
+  const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, base, dims, strides, box, estr,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) { rsst_set_error("cuTensorMapEncodeTiled (3D) failed (%d)", (int)r); return RSST_ECUDA; }
+  return RSST_OK;
+}
+
 static int make_tmap_2d(CUtensorMap* m, void* base, const Geom& g, int nv, int box_x, int box_y) {
   auto enc = tensor_map_encoder();
   if (!enc) { rsst_set_error("cuTensorMapEncodeTiled unavailable from the driver"); return RSST_ECUDA; }
@@ -229,6 +245,13 @@ extern "C" int rsst_init(rsst_handle** out, const rsst_config* cfg, void* stream
       if (rc != RSST_OK) goto fail;
     }
   }
+  if (cfg->precision == RSST_FP32_PERT && cfg->ndim == 3 && (cfg->vertical == -1 || cfg->vertical == 2)) {
+    h->use_tma3d = 1;
+    for (int b = 0; b < 2; ++b) {
+      rc = make_tmap_3d(&h->tmap[b], h->buf[b], h->g, nv, 40, 12);
+      if (rc != RSST_OK) goto fail;
+    }
+  }
   *out = h;
   return RSST_OK;
 fail:
@@ -311,6 +334,7 @@ static int run_steps(rsst_handle* h, double dt, int nsteps) {
     a.out = Us;
     if constexpr (sizeof(T) == 8) RC_TRY(rsst_launch_stage_fp64(a, h->stream));
     else if (h->use_tma2d) RC_TRY(rsst_launch_stage2d_tma(&h->tmap[0], a, h->stream));
+    else if (h->use_tma3d) RC_TRY(rsst_launch_stage3d_tma(&h->tmap[0], a, h->stream));
     else RC_TRY(rsst_launch_stage_fp32(a, h->stream));
     a.stage = 2;
     a.in = Us;
@@ -318,6 +342,7 @@ static int run_steps(rsst_handle* h, double dt, int nsteps) {
     a.out = U;
     if constexpr (sizeof(T) == 8) RC_TRY(rsst_launch_stage_fp64(a, h->stream));
     else if (h->use_tma2d) RC_TRY(rsst_launch_stage2d_tma(&h->tmap[1], a, h->stream));
+    else if (h->use_tma3d) RC_TRY(rsst_launch_stage3d_tma(&h->tmap[1], a, h->stream));
     else RC_TRY(rsst_launch_stage_fp32(a, h->stream));
     h->launches += 2;
     h->slot ^= 1;

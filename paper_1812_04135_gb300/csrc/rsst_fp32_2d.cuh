@@ -165,13 +165,14 @@ __device__ __forceinline__ bool tile2d_f(const CUtensorMap* tin, const TileRun& 
       st[id] = kp < r.tab_len ? r.tab[(size_t)f * r.tab_len + kp] : 0.0f;
     }
   }
-  if (!mbar_wait_bounded(bar, phase)) {
-    atomicOr(r.flag, RSST_FLAG_TIMEOUT);
+  // the give-up decision is taken by the whole block (no thread may leave
+  // while others wait at a barrier); a late copy gets one more bounded wait
+  if (__syncthreads_or(!mbar_wait_bounded(bar, phase))) {
+    if (tid == 0) atomicOr(r.flag, RSST_FLAG_TIMEOUT);
     mbar_wait_bounded(bar, phase);
     return false;
   }
   phase ^= 1u;
-  __syncthreads();
 
   // x faces
   const int nx = g.n[0], ny = g.n[1];

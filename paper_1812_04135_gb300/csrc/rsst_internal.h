@@ -99,6 +99,7 @@ int rsst_launch_sums_fp64(const double* U, const Geom& g, double* partial, doubl
 
 int rsst_launch_stage_fp32(const StageArgs<float>& a, cudaStream_t s);
 int rsst_launch_stage2d_tma(const CUtensorMap* tin, const StageArgs<float>& a, cudaStream_t s);
+int rsst_launch_stage3d_tma(const CUtensorMap* tin, const StageArgs<float>& a, cudaStream_t s);
 int rsst_launch_bgtab(const double* bg, int bg_len, const Geom& g, const Phys& p, float* tab, cudaStream_t s);
 int rsst_launch_pack_fp32(const double* src, float* dst, const Geom& g, const Phys& p, const double* bg,
                           int bg_len, cudaStream_t s);
@@ -129,6 +130,7 @@ struct rsst_handle {
   float* d_tab;         // background tables (float32 mode), or null
   PhysF pf;
   int use_tma2d;        // 2D float32 runs use the TMA-staged kernel
+  int use_tma3d;        // 3D float32 runs use the TMA z-march kernel
   CUtensorMap tmap[2];  // tensor maps of buf[0], buf[1] (TMA kernels)
   void* adj;            // adjoint checkpoints and work arrays, or null
   int slot;
