@@ -257,3 +257,30 @@ def random_smooth_state(ndim: int, n, xi: float = 7.0, variant: str = "pvs", see
     return _base(ndim, n, tuple(1.0 / v for v in n), gamma, xi, variant,
                  bc or ("periodic",) * ndim, grav=grav, U=_pack(rho, vel, p, gamma),
                  name="random_smooth")
+
+
+# ---------------------------------------------------------------------------
+# Linear entropy wave with velocity shear at 30 degrees (convergence study)
+# ---------------------------------------------------------------------------
+
+def linear_wave_2d(n: int, variant: str = "pvs", xi: float = 5.0, eps: float = 1e-5, p0: float = 1000.0,
+                   theta_deg: float = 30.0, gamma: float = 5.0 / 3.0) -> Dict:
+    """Domain [0, 1/cos t] x [0, 1/sin t], n x n cells, periodic; with
+    x_par = x cos t + y sin t: rho = 1 + eps sin(2 pi x_par), P = p0,
+    V_par = 1, V_perp = eps sin(2 pi x_par) (the test of the paper's linear
+    wave convergence study; after unit time the exact state returns)."""
+    th = math.radians(theta_deg)
+    lx, ly = 1.0 / math.cos(th), 1.0 / math.sin(th)
+    x = _centres(n, lx)
+    y = _centres(n, ly)
+    X, Y = np.meshgrid(x, y, indexing="xy")  # [ny, nx]
+    xp = X * math.cos(th) + Y * math.sin(th)
+    w = np.sin(2.0 * math.pi * xp)
+    rho = 1.0 + eps * w
+    vpar = np.ones_like(w)
+    vperp = eps * w
+    vx = vpar * math.cos(th) - vperp * math.sin(th)
+    vy = vpar * math.sin(th) + vperp * math.cos(th)
+    p = np.full_like(w, p0)
+    return _base(2, (n, n), (lx / n, ly / n), gamma, xi, variant, ("periodic", "periodic"),
+                 U=_pack(rho, [vx, vy], p, gamma), name="linear_wave_2d")
