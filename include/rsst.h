@@ -88,6 +88,9 @@ typedef struct rsst_config {
   int32_t reserved;
   const double* bg_rho;
   const double* bg_p;
+  double cmax;         /* > 0: state-dependent reduction xi = [1 + (a/cmax)^4]^(1/4)
+                        * (Eq. cx, Sec. 4.3) in c_tot and in f = 1 - 1/xi^2, per
+                        * face state and per cell; 0: the constant xi above */
 } rsst_config;
 
 typedef struct rsst_handle rsst_handle;

@@ -32,8 +32,8 @@ def step_vjp(U: torch.Tensor, lam: torch.Tensor, dt: float, prob: ro.Problem):
     Uc = U.detach().clone().requires_grad_(True)
     xi_t = torch.tensor(float(prob.xi), dtype=ro.DT, requires_grad=True)
     out = ro.ssp_rk2_step(Uc, dt, replace(prob, xi=xi_t))
-    gU, gxi = torch.autograd.grad(out, [Uc, xi_t], grad_outputs=lam)
-    return gU, float(gxi)
+    gU, gxi = torch.autograd.grad(out, [Uc, xi_t], grad_outputs=lam, allow_unused=True)
+    return gU, 0.0 if gxi is None else float(gxi)
 
 
 def stage_vjp(U: torch.Tensor, lam: torch.Tensor, prob: ro.Problem):
@@ -41,8 +41,8 @@ def stage_vjp(U: torch.Tensor, lam: torch.Tensor, prob: ro.Problem):
     Uc = U.detach().clone().requires_grad_(True)
     xi_t = torch.tensor(float(prob.xi), dtype=ro.DT, requires_grad=True)
     out = ro.rhs(Uc, replace(prob, xi=xi_t))
-    gU, gxi = torch.autograd.grad(out, [Uc, xi_t], grad_outputs=lam)
-    return gU, float(gxi)
+    gU, gxi = torch.autograd.grad(out, [Uc, xi_t], grad_outputs=lam, allow_unused=True)
+    return gU, 0.0 if gxi is None else float(gxi)
 
 
 def adjoint_run(U0: torch.Tensor, prob: ro.Problem, nsteps: int, dt: float, every: int,
@@ -74,7 +74,7 @@ def adjoint_run(U0: torch.Tensor, prob: ro.Problem, nsteps: int, dt: float, ever
         Ue = Uc
         for _ in range(s0, s1):
             Ue = ro.ssp_rk2_step(Ue, dt, p)
-        gU, gxi = torch.autograd.grad(Ue, [Uc, xi_t], grad_outputs=lam)
+        gU, gxi = torch.autograd.grad(Ue, [Uc, xi_t], grad_outputs=lam, allow_unused=True)
         lam = gU.detach()
-        dxi += float(gxi)
+        dxi += 0.0 if gxi is None else float(gxi)
     return J, U, lam, dxi

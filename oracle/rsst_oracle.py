@@ -83,6 +83,7 @@ class Problem:
     vertical: int = -1
     bg_rho: Optional[torch.Tensor] = None
     bg_p: Optional[torch.Tensor] = None
+    cmax: Optional[float] = None  # C_max law (Eq. cx) instead of a constant xi
 
     @property
     def nvar(self) -> int:
@@ -118,10 +119,17 @@ def _speed(v2: torch.Tensor) -> torch.Tensor:
     return torch.sqrt(torch.where(pos, v2, torch.ones_like(v2))) * pos
 
 
-def c_tot(U: torch.Tensor, gamma: float, xi) -> torch.Tensor:
+def xi_of(a2: torch.Tensor, xi, cmax=None):
+    """Reduction rate: the constant xi, or xi = [1 + (a/C_max)^4]^(1/4) (Eq. cx, Sec. 4.3)."""
+    if cmax is None:
+        return xi
+    return (1.0 + (a2 / (cmax * cmax)) ** 2) ** 0.25
+
+
+def c_tot(U: torch.Tensor, gamma: float, xi, cmax=None) -> torch.Tensor:
     """Approximate RSST characteristic speed |V| + a/xi (Sec. 4.2)."""
     rho, V, v2, P, a2 = primitives(U, gamma)
-    return _speed(v2) + torch.sqrt(a2) / xi
+    return _speed(v2) + torch.sqrt(a2) / xi_of(a2, xi, cmax)
 
 
 def physical_flux(U: torch.Tensor, d: int, gamma: float) -> torch.Tensor:
@@ -155,10 +163,11 @@ def mc_limiter(a: torch.Tensor, b: torch.Tensor) -> torch.Tensor:
     return torch.where(a * b > 0, s, torch.zeros_like(s))
 
 
-def llf_flux(UL: torch.Tensor, UR: torch.Tensor, d: int, gamma: float, xi) -> torch.Tensor:
-    """Local Lax-Friedrichs flux with alpha = max(c_tot(U_L), c_tot(U_R)) (Sec. 4.2, step 4)."""
-    cl = c_tot(UL, gamma, xi)
-    cr = c_tot(UR, gamma, xi)
+def llf_flux(UL: torch.Tensor, UR: torch.Tensor, d: int, gamma: float, xi, cmax=None) -> torch.Tensor:
+    """Local Lax-Friedrichs flux with alpha = max(c_tot(U_L), c_tot(U_R)) (Sec. 4.2, step 4);
+    under the C_max law xi is evaluated on each side's own state."""
+    cl = c_tot(UL, gamma, xi, cmax)
+    cr = c_tot(UR, gamma, xi, cmax)
     alpha = torch.where(cl >= cr, cl, cr)
     return 0.5 * (physical_flux(UL, d, gamma) + physical_flux(UR, d, gamma)) - 0.5 * alpha * (UR - UL)
 
@@ -217,7 +226,7 @@ def face_fluxes(U: torch.Tensor, d: int, prob: Problem) -> torch.Tensor:
     sigma = mc_limiter(mid - left, right - mid)          # cells -1 .. n
     UL = (mid + 0.5 * sigma).narrow(ax, 0, n + 1)        # face i+1/2 uses cell i
     UR = (mid - 0.5 * sigma).narrow(ax, 1, n + 1)        # and cell i+1
-    return llf_flux(UL, UR, d, prob.gamma, prob.xi)
+    return llf_flux(UL, UR, d, prob.gamma, prob.xi, prob.cmax)
 
 
 def euler_tendency(U: torch.Tensor, prob: Problem) -> torch.Tensor:
@@ -270,11 +279,17 @@ def correction_vector(U: torch.Tensor, variant: int, gamma: float):
     raise ValueError(f"no correction vector for variant {variant}")
 
 
-def rsst_correct(U: torch.Tensor, dU: torch.Tensor, variant: int, gamma: float, xi) -> torch.Tensor:
-    """Reduced tendency dU - (1 - 1/xi^2) s r (Sec. 4.2 steps 6-7; Eq. pvs_dt and App. A)."""
+def rsst_correct(U: torch.Tensor, dU: torch.Tensor, variant: int, gamma: float, xi, cmax=None) -> torch.Tensor:
+    """Reduced tendency dU - (1 - 1/xi^2) s r (Sec. 4.2 steps 6-7; Eq. pvs_dt and App. A);
+    under the C_max law xi is that of the cell's own sound speed."""
     if variant == EULER:
         return dU
-    f = 1.0 - 1.0 / (xi * xi)
+    if cmax is None:
+        f = 1.0 - 1.0 / (xi * xi)
+    else:
+        a2 = primitives(U, gamma)[4]
+        xc = xi_of(a2, xi, cmax)
+        f = 1.0 - 1.0 / (xc * xc)
     which, r = correction_vector(U, variant, gamma)
     s = pressure_tendency(U, dU, gamma) if which == "P" else dU[0]
     return torch.stack([dU[k] - f * s * r[k] for k in range(U.shape[0])])
@@ -297,7 +312,7 @@ def has_gravity(prob: Problem) -> bool:
 
 def rhs(U: torch.Tensor, prob: Problem) -> torch.Tensor:
     """L(U): Euler tendency, RSST correction, then the external force."""
-    out = rsst_correct(U, euler_tendency(U, prob), prob.variant, prob.gamma, prob.xi)
+    out = rsst_correct(U, euler_tendency(U, prob), prob.variant, prob.gamma, prob.xi, prob.cmax)
     if has_gravity(prob):
         out = out + gravity_source(U, prob)
     return out
@@ -310,7 +325,7 @@ def rhs(U: torch.Tensor, prob: Problem) -> torch.Tensor:
 def cfl_dt(U: torch.Tensor, prob: Problem) -> float:
     """dt = C / max_cells sum_d c_tot / dx_d with C = prob.cfl (0.4 in the paper)."""
     with torch.no_grad():
-        c = c_tot(U, prob.gamma, float(prob.xi))
+        c = c_tot(U, prob.gamma, float(prob.xi), prob.cmax)
         rate = sum(c / prob.dx[d] for d in range(prob.ndim))
         return float(prob.cfl / rate.max())
 

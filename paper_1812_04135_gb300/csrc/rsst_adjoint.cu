@@ -87,7 +87,11 @@ __device__ __forceinline__ void euler_flux_T(const T (&q)[NV], const Phys& p, T 
     v2 = v2 + v[e] * v[e];
   }
   const T P = p.gm1 * (q[NV - 1] - 0.5 * (rho * v2));
-  c = speed_T(v2) + dsqrt(p.gamma * P / rho) * inv_xi;
+  const T a2 = p.gamma * P / rho;
+  if (p.use_cmax)  // C_max law (Eq. cx): a/xi = sqrt(a^2 / sqrt(1 + a^4/C^4))
+    c = speed_T(v2) + dsqrt(a2 / dsqrt(1.0 + (a2 * a2) * p.inv_cmax4));
+  else
+    c = speed_T(v2) + dsqrt(a2) * inv_xi;
   F[0] = q[1 + D];
   for (int e = 0; e < ND; ++e) F[1 + e] = (e == D) ? q[1 + e] * v[D] + P : q[1 + e] * v[D];
   F[NV - 1] = (q[NV - 1] + P) * v[D];
@@ -146,7 +150,9 @@ __device__ __forceinline__ void rhs_T(const T (&q)[NV], const T (&dU)[NV], T f, 
       if (var == RSST_DVS) { rv = q[0] * 0.0 + 1.0; has_rv = true; }
       rE = (var == RSST_DVS ? (e_int + P + kin) : (e_int + P - kin)) / rho;
     }
-    const T fs = f * s;
+    // f = 1 - 1/xi^2: constant, or from the cell's a^2 under the C_max law
+    const T fc = p.use_cmax ? 1.0 - 1.0 / dsqrt(1.0 + ((p.gamma * P / rho) * (p.gamma * P / rho)) * p.inv_cmax4) : f;
+    const T fs = fc * s;
     L[0] = L[0] - fs * r0;
     if (has_rv)
       for (int e = 0; e < ND; ++e) L[1 + e] = L[1 + e] - fs * (rv * v[e]);

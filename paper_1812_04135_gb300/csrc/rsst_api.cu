@@ -99,6 +99,7 @@ static int validate(const rsst_config* c) {
   if (!(c->xi >= 1.0) || !std::isfinite(c->xi)) { rsst_set_error("xi must be finite and >= 1 (got %g)", c->xi); return RSST_EINVAL; }
   if (!(c->gamma > 1.0)) { rsst_set_error("gamma must be > 1"); return RSST_EINVAL; }
   if (!(c->cfl > 0.0)) { rsst_set_error("cfl must be > 0"); return RSST_EINVAL; }
+  if (!(c->cmax >= 0.0) || !std::isfinite(c->cmax)) { rsst_set_error("cmax must be >= 0 (0: constant xi)"); return RSST_EINVAL; }
   if (c->vertical < -1 || c->vertical >= c->ndim) { rsst_set_error("vertical axis %d invalid", c->vertical); return RSST_EINVAL; }
   if (c->vertical >= 0 && (!c->bg_rho || !c->bg_p)) { rsst_set_error("background profiles required when vertical >= 0"); return RSST_EINVAL; }
   int64_t cells = 1;
@@ -129,6 +130,8 @@ static void make_physf(const Phys* p, PhysF* f) {
   f->inv_gm1 = (float)p->inv_gm1;
   f->inv_xi = (float)p->inv_xi;
   f->f = (float)p->f;
+  f->inv_cmax4 = (float)p->inv_cmax4;
+  f->use_cmax = p->use_cmax;
   for (int d = 0; d < 3; ++d) {
     f->grav[d] = (float)p->grav[d];
     f->inv_dx[d] = (float)p->inv_dx[d];
@@ -145,6 +148,8 @@ static void make_phys(const rsst_config* c, Phys* p) {
   p->xi = c->xi;
   p->inv_xi = 1.0 / c->xi;
   p->f = 1.0 - 1.0 / (c->xi * c->xi);
+  p->use_cmax = c->cmax > 0.0;
+  p->inv_cmax4 = p->use_cmax ? 1.0 / (c->cmax * c->cmax * c->cmax * c->cmax) : 0.0;
   p->cfl = c->cfl;
   p->variant = c->variant;
   p->vertical = c->vertical;

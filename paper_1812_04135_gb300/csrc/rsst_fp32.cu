@@ -59,7 +59,7 @@ __global__ void bgtab_kernel(const double* __restrict__ bg, int L, Phys p, float
     face(k, qL, qR);
     const double PL = p.gm1 * qL[NV - 1], PR = p.gm1 * qR[NV - 1];
     const double aL = sqrt(p.gamma * PL / qL[0]), aR = sqrt(p.gamma * PR / qR[0]);
-    const double cL = aL * p.inv_xi, cR = aR * p.inv_xi;
+    const double cL = sound_over_xi(p.gamma * PL / qL[0], p), cR = sound_over_xi(p.gamma * PR / qR[0], p);
     put(TB_FRHOL, qL[0]);
     put(TB_FRHOR, qR[0]);
     put(TB_FEL, qL[NV - 1]);
@@ -196,11 +196,12 @@ __device__ __forceinline__ void face_pass_f(const float* __restrict__ su, float*
         qR[v] = u0[v] - 0.5f * sr;
       }
       float FL[NV], FR[NV], cL, cR, dcL, dcR;
+      const float gdiff = st[TB_FG * C::SV + rR], al0 = st[TB_FALPHA * C::SV + rR];
+      const float c0L = gdiff >= 0.0f ? al0 : al0 + gdiff, c0R = gdiff >= 0.0f ? al0 - gdiff : al0;
       pert_flux_f<NV, D, true>(qL, st[TB_FRHOL * C::SV + rR], st[TB_FPL * C::SV + rR], st[TB_FHL * C::SV + rR],
-                               st[TB_FAL * C::SV + rR], pf, FL, cL, dcL);
+                               st[TB_FAL * C::SV + rR], pf, FL, cL, dcL, c0L);
       pert_flux_f<NV, D, true>(qR, st[TB_FRHOR * C::SV + rR], st[TB_FPR * C::SV + rR], st[TB_FHR * C::SV + rR],
-                               st[TB_FAR * C::SV + rR], pf, FR, cR, dcR);
-      const float gdiff = st[TB_FG * C::SV + rR];
+                               st[TB_FAR * C::SV + rR], pf, FR, cR, dcR, c0R);
       const float dalpha = gdiff >= 0.0f ? fmaxf(dcL, dcR - gdiff) : fmaxf(dcL + gdiff, dcR);
       const float alpha = st[TB_FALPHA * C::SV + rR] + dalpha;
 #pragma unroll
@@ -350,7 +351,7 @@ __global__ void __launch_bounds__(NT) stage_fp32_kernel(const StageArgs<float> a
         rv = var == RSST_DVS ? 1.0f : 0.0f;
         rE = (var == RSST_DVS ? (e_int + P + kin) : (e_int + P - kin)) * ir;
       }
-      const float fs = pf.f * s;
+      const float fs = f_of_f(pf.gamma * P * ir, pf) * s;
       L[0] -= fs * r0;
 #pragma unroll
       for (int e = 0; e < ND; ++e) L[1 + e] -= fs * (rv * vel[e]);
@@ -386,7 +387,7 @@ __global__ void __launch_bounds__(NT) stage_fp32_kernel(const StageArgs<float> a
       }
       const float Pn = P0 + pf.gm1 * (u[NV - 1] - 0.5f * mw);
       const bool ok = fin && rn > 0.0f && Pn > 0.0f;
-      if (ok) rmax = fmaxf(rmax, (sqrtf(w2) + sqrtf(pf.gamma * Pn * irn) * pf.inv_xi) * pf.sum_inv_dx);
+      if (ok) rmax = fmaxf(rmax, (sqrtf(w2) + sound_over_xi_f(pf.gamma * Pn * irn, pf)) * pf.sum_inv_dx);
       ok_all = ok_all && ok;
     }
     store_mirror_ghosts<float, NV>(a.out, g, p, i, j, k, u);
@@ -498,7 +499,7 @@ __global__ void __launch_bounds__(256) cfl_fp32_kernel(const float* __restrict__
     }
     const float Pn = P0 + pf.gm1 * (u[NV - 1] - 0.5f * mw);
     const bool ok = fin && rn > 0.0f && Pn > 0.0f;
-    if (ok) rmax = fmaxf(rmax, (sqrtf(w2) + sqrtf(pf.gamma * Pn * irn) * pf.inv_xi) * pf.sum_inv_dx);
+    if (ok) rmax = fmaxf(rmax, (sqrtf(w2) + sound_over_xi_f(pf.gamma * Pn * irn, pf)) * pf.sum_inv_dx);
     ok_all = ok_all && ok;
   }
   if (!ok_all) atomicOr(flag, 1u);

@@ -120,11 +120,12 @@ __device__ __forceinline__ void t2_yflux(const float (&u0)[4], const float (&s0)
     for (int v = 0; v < NV; ++v) F[v] = 0.5f * (FL[v] + FR[v]) - 0.5f * alpha * (qR[v] - qL[v]);
   } else {
     float dcL, dcR;
+    const float gdiff = st[TB_FG * T2::SYP + rf], al0 = st[TB_FALPHA * T2::SYP + rf];
+    const float c0L = gdiff >= 0.0f ? al0 : al0 + gdiff, c0R = gdiff >= 0.0f ? al0 - gdiff : al0;
     pert_flux_f<NV, 1, true>(qL, st[TB_FRHOL * T2::SYP + rf], st[TB_FPL * T2::SYP + rf], st[TB_FHL * T2::SYP + rf],
-                             st[TB_FAL * T2::SYP + rf], pf, FL, cL, dcL);
+                             st[TB_FAL * T2::SYP + rf], pf, FL, cL, dcL, c0L);
     pert_flux_f<NV, 1, true>(qR, st[TB_FRHOR * T2::SYP + rf], st[TB_FPR * T2::SYP + rf], st[TB_FHR * T2::SYP + rf],
-                             st[TB_FAR * T2::SYP + rf], pf, FR, cR, dcR);
-    const float gdiff = st[TB_FG * T2::SYP + rf];
+                             st[TB_FAR * T2::SYP + rf], pf, FR, cR, dcR, c0R);
     const float dalpha = gdiff >= 0.0f ? fmaxf(dcL, dcR - gdiff) : fmaxf(dcL + gdiff, dcR);
     const float alpha = st[TB_FALPHA * T2::SYP + rf] + dalpha;
     const float jr = st[TB_FDRHO * T2::SYP + rf], je = st[TB_FDE * T2::SYP + rf];

@@ -101,11 +101,12 @@ __device__ __forceinline__ void t3_zflux(const float (&u0)[5], const float (&s0)
   } else {
     constexpr int R = T3::TROWS;
     float dcL, dcR;
+    const float gdiff = st[TB_FG * R + rf], al0 = st[TB_FALPHA * R + rf];
+    const float c0L = gdiff >= 0.0f ? al0 : al0 + gdiff, c0R = gdiff >= 0.0f ? al0 - gdiff : al0;
     pert_flux_f<NV, 2, true>(qL, st[TB_FRHOL * R + rf], st[TB_FPL * R + rf], st[TB_FHL * R + rf], st[TB_FAL * R + rf],
-                             pf, FL, cL, dcL);
+                             pf, FL, cL, dcL, c0L);
     pert_flux_f<NV, 2, true>(qR, st[TB_FRHOR * R + rf], st[TB_FPR * R + rf], st[TB_FHR * R + rf], st[TB_FAR * R + rf],
-                             pf, FR, cR, dcR);
-    const float gdiff = st[TB_FG * R + rf];
+                             pf, FR, cR, dcR, c0R);
     const float dalpha = gdiff >= 0.0f ? fmaxf(dcL, dcR - gdiff) : fmaxf(dcL + gdiff, dcR);
     const float alpha = st[TB_FALPHA * R + rf] + dalpha;
     const float jr = st[TB_FDRHO * R + rf], je = st[TB_FDE * R + rf];

@@ -30,6 +30,8 @@ struct Geom {
 struct Phys {
   double gamma, gm1, inv_gm1, hgm1;  // hgm1 = (gamma - 1)/2
   double xi, inv_xi, f;  // f = 1 - 1/xi^2
+  double inv_cmax4;      // 1/C_max^4 (state-dependent xi, Eq. cx), used if use_cmax
+  int use_cmax;
   double cfl;
   double grav[3];
   double inv_dx[3];
@@ -43,6 +45,8 @@ struct Phys {
 // Float32 copies of the constants used by the float32 kernels.
 struct PhysF {
   float gamma, gm1, inv_gm1, inv_xi, f;
+  float inv_cmax4;
+  int use_cmax;
   float grav[3];
   float inv_dx[3];
   float sum_inv_dx;

@@ -42,6 +42,16 @@ __device__ __forceinline__ float mc_linear_f(int br, float a, float b) {
   return br == 0 ? 0.0f : (br == 1 ? 2.0f * a : (br == 2 ? 2.0f * b : 0.5f * (a + b)));
 }
 
+// a/xi and f = 1 - 1/xi^2 from a^2 (constant xi, or the C_max law, Eq. cx).
+__device__ __forceinline__ float sound_over_xi_f(float a2, const PhysF& p) {
+  if (p.use_cmax) return sqrtf(a2 / sqrtf(fmaf(a2 * a2, p.inv_cmax4, 1.0f)));
+  return sqrtf(a2) * p.inv_xi;
+}
+__device__ __forceinline__ float f_of_f(float a2, const PhysF& p) {
+  if (p.use_cmax) return 1.0f - 1.0f / sqrtf(fmaf(a2 * a2, p.inv_cmax4, 1.0f));
+  return p.f;
+}
+
 // Full-state Euler flux and c_tot along D in float32 (no background).
 template <int NV, int D>
 __device__ __forceinline__ void euler_flux_f(const float (&q)[NV], const PhysF& p, float (&F)[NV], float& c) {
@@ -56,7 +66,7 @@ __device__ __forceinline__ void euler_flux_f(const float (&q)[NV], const PhysF& 
     v2 += v[e] * v[e];
   }
   const float P = p.gm1 * (q[NV - 1] - 0.5f * rho * v2);
-  c = sqrtf(v2) + sqrtf(p.gamma * P * ir) * p.inv_xi;
+  c = sqrtf(v2) + sound_over_xi_f(p.gamma * P * ir, p);
   F[0] = q[1 + D];
 #pragma unroll
   for (int e = 0; e < ND; ++e) F[1 + e] = q[1 + e] * v[D] + (e == D ? P : 0.0f);
@@ -64,10 +74,11 @@ __device__ __forceinline__ void euler_flux_f(const float (&q)[NV], const PhysF& 
 }
 
 // Perturbation flux F(U0 + q1) - F(U0) along D, the full c_tot, and c - c0.
-// Background face values: rho0, E0, P0 = (gamma-1) E0, H0 = E0 + P0, a0.
+// Background face values: rho0, E0, P0 = (gamma-1) E0, H0 = E0 + P0, its
+// sound speed a0 and speed c0 = a0/xi(a0) (c0 used with the C_max law).
 template <int NV, int D, bool WANT_DC>
 __device__ __forceinline__ void pert_flux_f(const float (&q1)[NV], float rho0, float P0, float H0, float a0,
-                                            const PhysF& p, float (&F)[NV], float& c, float& dc) {
+                                            const PhysF& p, float (&F)[NV], float& c, float& dc, float c0 = 0.0f) {
   constexpr int ND = NV - 2;
   const float rho = rho0 + q1[0];
   const float ir = 1.0f / rho;
@@ -80,12 +91,19 @@ __device__ __forceinline__ void pert_flux_f(const float (&q1)[NV], float rho0, f
     mv += q1[1 + e] * v[e];
   }
   const float P1 = p.gm1 * (q1[NV - 1] - 0.5f * mv);
-  const float a = sqrtf(p.gamma * (P0 + P1) * ir);
+  const float a2 = p.gamma * (P0 + P1) * ir;
   const float vm = sqrtf(v2);
-  c = vm + a * p.inv_xi;
-  if (WANT_DC) {
-    const float da2 = p.gamma * (P1 * rho0 - P0 * q1[0]) * ir / rho0;
-    dc = vm + (da2 / (a + a0)) * p.inv_xi;
+  if (p.use_cmax) {
+    const float g = sound_over_xi_f(a2, p);
+    c = vm + g;
+    if (WANT_DC) dc = vm + (g - c0);  // multiplies only the background face jump
+  } else {
+    const float a = sqrtf(a2);
+    c = vm + a * p.inv_xi;
+    if (WANT_DC) {
+      const float da2 = p.gamma * (P1 * rho0 - P0 * q1[0]) * ir / rho0;
+      dc = vm + (da2 / (a + a0)) * p.inv_xi;
+    }
   }
   F[0] = q1[1 + D];
 #pragma unroll
@@ -129,6 +147,7 @@ __device__ __forceinline__ void cell_update_f(const float (&q)[NV], float (&L)[N
   }
   const float P = P0 + pf.gm1 * (q[NV - 1] - 0.5f * mv);
   if (variant != RSST_EULER) {
+    const float fcell = f_of_f(pf.gamma * P * ir, pf);
     const float e_int = P * pf.inv_gm1;
     const float kin = 0.5f * mv;
     float s, r0, rv, rE;
@@ -148,7 +167,7 @@ __device__ __forceinline__ void cell_update_f(const float (&q)[NV], float (&L)[N
       rv = variant == RSST_DVS ? 1.0f : 0.0f;
       rE = (variant == RSST_DVS ? (e_int + P + kin) : (e_int + P - kin)) * ir;
     }
-    const float fs = pf.f * s;
+    const float fs = fcell * s;
     L[0] -= fs * r0;
 #pragma unroll
     for (int e = 0; e < ND; ++e) L[1 + e] -= fs * (rv * vel[e]);
@@ -184,7 +203,7 @@ __device__ __forceinline__ void cell_update_f(const float (&q)[NV], float (&L)[N
     }
     const float Pn = P0 + pf.gm1 * (u[NV - 1] - 0.5f * mw);
     ok = fin && rn > 0.0f && Pn > 0.0f;
-    if (ok) rate = (sqrtf(w2) + sqrtf(pf.gamma * Pn * irn) * pf.inv_xi) * pf.sum_inv_dx;
+    if (ok) rate = (sqrtf(w2) + sound_over_xi_f(pf.gamma * Pn * irn, pf)) * pf.sum_inv_dx;
   }
 }
 

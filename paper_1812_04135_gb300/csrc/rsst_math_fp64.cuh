@@ -22,6 +22,18 @@ __device__ __forceinline__ double rcp_nr(double x) {
   return fma(y, e, y);
 }
 
+// Effective sound speed a/xi from a^2 and the factor f = 1 - 1/xi^2: constant
+// xi, or the C_max law xi = [1 + (a/C_max)^4]^(1/4) (Eq. cx, Sec. 4.3), for
+// which a/xi = sqrt(a^2 / sqrt(w)) and f = 1 - 1/sqrt(w), w = 1 + a^4/C_max^4.
+__device__ __forceinline__ double sound_over_xi(double a2, const Phys& p) {
+  if (p.use_cmax) return sqrt(a2 / sqrt(fma(a2 * a2, p.inv_cmax4, 1.0)));
+  return sqrt(a2) * p.inv_xi;
+}
+__device__ __forceinline__ double f_of(double a2, const Phys& p) {
+  if (p.use_cmax) return 1.0 - 1.0 / sqrt(fma(a2 * a2, p.inv_cmax4, 1.0));
+  return p.f;
+}
+
 // Half the Euler flux along dimension D, F/2, and the approximate RSST
 // characteristic speed c_tot = |V| + a/xi of one state (Eq. pvs_dt0; Sec. 4.2).
 template <int NV, int D>
@@ -38,8 +50,7 @@ __device__ __forceinline__ void euler_flux(const double (&q)[NV], const Phys& p,
     v2 += v[e] * v[e];
   }
   const double P = p.gm1 * q[NV - 1] - p.hgm1 * (rho * v2);
-  const double a = sqrt(p.gamma * P * ir);
-  c = sqrt(v2) + a * p.inv_xi;
+  c = sqrt(v2) + sound_over_xi(p.gamma * P * ir, p);
   // half fluxes: the LLF average of the two sides needs F/2
   const double hv = 0.5 * v[D];
   F[0] = 0.5 * q[1 + D];
@@ -125,7 +136,7 @@ __device__ __forceinline__ void rsst_rhs(const double (&q)[NV], double (&dU)[NV]
       rv = (var == RSST_DVS) ? 1.0 : 0.0;
       rE = (var == RSST_DVS ? (e_int + P + kin) : (e_int + P - kin)) * ir;
     }
-    const double fs = p.f * s;
+    const double fs = f_of(p.gamma * P * ir, p) * s;
     dU[0] -= fs * r0;
 #pragma unroll
     for (int e = 0; e < ND; ++e) dU[1 + e] -= fs * (rv * v[e]);
@@ -158,7 +169,7 @@ __device__ __forceinline__ double cfl_rate(const double (&q)[NV], const Phys& p,
   }
   const double P = p.gm1 * (q[NV - 1] - 0.5 * rho * v2);
   ok = fin && rho > 0.0 && P > 0.0;
-  const double c = sqrt(v2) + sqrt(p.gamma * P * ir) * p.inv_xi;
+  const double c = sqrt(v2) + sound_over_xi(p.gamma * P * ir, p);
   return c * p.sum_inv_dx;
 }
 

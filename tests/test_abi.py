@@ -37,7 +37,7 @@ def test_every_declared_symbol_is_exported(L):
 
 
 def test_config_layout(L):
-    assert L.rsst_config_size() == 136
+    assert L.rsst_config_size() == 144
 
 
 @pytest.mark.parametrize("bad", [dict(ndim=4), dict(xi=0.5), dict(gamma=1.0), dict(variant="bogus"),

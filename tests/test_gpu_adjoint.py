@@ -172,3 +172,19 @@ def test_adjoint_workload_full_size():
     print("dJ/dxi adjoint %.10e  central difference %.10e" % (dxi, fdx))
     assert dxi == pytest.approx(fdx, rel=1e-2)
     s.close()
+
+
+@pytest.mark.parametrize("var", ["pvs", "dms"])
+def test_one_step_vjp_cmax(var):
+    """Adjoint under the C_max law: the state gradient includes d xi / d a;
+    xi is not a parameter then, so dJ/dxi is zero."""
+    w = inputs.polytrope_2d(20, 24, xi=1.0, contrast=20.0, amp=1e-2)
+    w["variant"] = var
+    w["cmax"] = 0.05
+    prob, U = problem_from(w)
+    dt = 0.5 * ro.cfl_dt(U, prob)
+    lam = torch.tensor(inputs.uniform_pm1(98, U.numel()).reshape(U.shape))
+    gU, _ = adj.step_vjp(U, lam, dt, prob)
+    _, got, dxi = gpu_adjoint(w, dt, 1, 1, lam)
+    assert close(got, gU, 1e-10)
+    assert dxi == 0.0

@@ -114,3 +114,11 @@ def test_sound_wave_and_contact_1d():
     check(w, 100)
     w = inputs.contact_1d(256, xi=10.0, variant="pvs")
     check(w, 10)
+
+
+def test_cmax_law_float32():
+    for w in (inputs.random_smooth_state(2, (70, 37), xi=1.0, variant="pvs"),
+              inputs.polytrope_2d(40, 70, xi=1.0, contrast=20.0, amp=1e-3),
+              inputs.polytrope_3d(20, 12, 40, xi=1.0, amp=1e-3, contrast=20.0)):
+        w["cmax"] = 0.05
+        check(w, 5, what=w["name"])

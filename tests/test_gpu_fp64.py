@@ -193,3 +193,18 @@ def test_float64_helpers_against_cuda():
     MC limiter identical to the direct float64 form."""
     ulp, bad = rsst.rsst_math_selftest(1 << 20)
     assert ulp <= 1.0 and bad == 0, (ulp, bad)
+
+
+@pytest.mark.parametrize("ndim", [1, 2, 3])
+def test_cmax_law(ndim):
+    """State-dependent xi = [1 + (a/C_max)^4]^(1/4) (Eq. cx) in c_tot and f."""
+    for var, bc, grav in (("pvs", None, (0.0, 0.0, 0.0)), ("dms", ("reflect",) * ndim, (0.2, -0.5, 0.3))):
+        w = inputs.random_smooth_state(ndim, SIZES[ndim], xi=1.0, variant=var, bc=bc, grav=grav)
+        w["cmax"] = 0.35
+        _assert_close(gpu_run(w, 4), oracle_run(w, 4), w["gamma"], what=(ndim, var))
+
+
+def test_cmax_stratified_background():
+    w = inputs.polytrope_2d(40, 70, xi=1.0, contrast=20.0, amp=1e-2)
+    w["cmax"] = 0.05
+    _assert_close(gpu_run(w, 6), oracle_run(w, 6), w["gamma"])
