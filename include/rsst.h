@@ -125,6 +125,10 @@ int rsst_step(rsst_handle* h, double dt, int nsteps);
  * current state).  Synchronous. */
 int rsst_dt(rsst_handle* h, double* dt_out);
 
+/* Simulated time: the sum of the dt of the steps taken since the last
+ * rsst_set_state (accumulated on the device).  Synchronous. */
+int rsst_time(rsst_handle* h, double* t);
+
 /* Wait for queued work; RSST_ENONPHYSICAL if a step flagged the state. */
 int rsst_sync(rsst_handle* h);
 

@@ -292,6 +292,7 @@ extern "C" int rsst_set_state(rsst_handle* h, const double* U, int on_host) {
     RC_TRY(rsst_launch_pack_fp64(src, (double*)h->buf[0], h->g, h->p, h->d_bg, h->bg_len, h->stream));
   CUDA_TRY(cudaMemsetAsync(h->d_flag, 0, sizeof(unsigned int), h->stream));
   CUDA_TRY(cudaMemsetAsync(h->d_scal + h->slot, 0, sizeof(double), h->stream));
+  CUDA_TRY(cudaMemsetAsync(h->d_scal + 3, 0, sizeof(double), h->stream));  // simulated time
   if (f32)
     RC_TRY(rsst_launch_cfl_fp32((const float*)h->buf[0], h->g, h->p, h->pf, h->d_tab, h->bg_len, h->d_scal + h->slot,
                                 h->d_flag, h->stream));
@@ -373,6 +374,14 @@ extern "C" int rsst_dt(rsst_handle* h, double* dt_out) {
   CUDA_TRY(cudaStreamSynchronize(h->stream));
   const double cmax = h->h_small[0];
   *dt_out = h->p.cfl / cmax;
+  return check_flag(h);
+}
+
+extern "C" int rsst_time(rsst_handle* h, double* t) {
+  if (!h || !t) { rsst_set_error("NULL argument"); return RSST_EINVAL; }
+  CUDA_TRY(cudaMemcpyAsync(h->h_small, h->d_scal + 3, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  CUDA_TRY(cudaStreamSynchronize(h->stream));
+  *t = h->h_small[0];
   return check_flag(h);
 }
 

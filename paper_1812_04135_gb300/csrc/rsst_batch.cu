@@ -65,6 +65,7 @@ __global__ void __launch_bounds__(C::NT) batch_stage_kernel(const BatchRun* __re
       if (stage == 1 && t == tile_begin[lo]) {
         br.scal[slot ^ 1] = 0.0;
         br.scal[2] = dtd;
+        br.scal[3] += dtd;
       }
     }
     __syncthreads();

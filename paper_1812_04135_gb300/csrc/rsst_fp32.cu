@@ -284,6 +284,7 @@ __global__ void __launch_bounds__(NT) stage_fp32_kernel(const StageArgs<float> a
   if (a.stage == 1 && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x == 0) {
     a.scal[a.slot ^ 1] = 0.0;
     a.scal[2] = dtd;
+    a.scal[3] += dtd;
   }
   float rmax = 0.0f;
   bool ok_all = true;

@@ -42,6 +42,7 @@ __global__ void __launch_bounds__(T2::NT, 2) stage2d_tma_kernel(const __grid_con
     if (a.stage == 1 && blockIdx.x == 0 && blockIdx.y == 0) {
       a.scal[a.slot ^ 1] = 0.0;
       a.scal[2] = dtd;
+      a.scal[3] += dtd;
     }
     mbar_init(bar, 1);
     fence_mbar_init();

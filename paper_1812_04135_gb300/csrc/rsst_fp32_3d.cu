@@ -146,6 +146,7 @@ __global__ void __launch_bounds__(T3::NT, 2) stage3d_tma_kernel(const __grid_con
     if (a.stage == 1 && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0) {
       a.scal[a.slot ^ 1] = 0.0;
       a.scal[2] = dtd;
+      a.scal[3] += dtd;
     }
     for (int s = 0; s < T3::NS; ++s) mbar_init(&bar[s], 1);
     fence_mbar_init();

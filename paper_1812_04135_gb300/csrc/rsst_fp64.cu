@@ -179,6 +179,7 @@ __global__ void __launch_bounds__(NT) stage_fp64_kernel(const StageArgs<double> 
   if (a.stage == 1 && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x == 0) {
     a.scal[a.slot ^ 1] = 0.0;
     a.scal[2] = dt;
+    a.scal[3] += dt;
   }
   double rmax = 0.0;
   bool ok_all = true;

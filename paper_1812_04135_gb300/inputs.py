@@ -284,3 +284,38 @@ def linear_wave_2d(n: int, variant: str = "pvs", xi: float = 5.0, eps: float = 1
     p = np.full_like(w, p0)
     return _base(2, (n, n), (lx / n, ly / n), gamma, xi, variant, ("periodic", "periodic"),
                  U=_pack(rho, [vx, vy], p, gamma), name="linear_wave_2d")
+
+
+# ---------------------------------------------------------------------------
+# Rayleigh-Taylor instability (the paper's RT test: printed initial data)
+# ---------------------------------------------------------------------------
+
+def rt_column_mass(y: np.ndarray, rho1: float = 1.0, rho2: float = 10.0, L: float = 0.025) -> np.ndarray:
+    """Mass per unit area above height y (to y = 1) of the unperturbed profile,
+    the closed form printed with the RT test."""
+    def lncosh2(z):  # ln(e^z + e^-z), written stably
+        z = np.abs(z)
+        return z + np.log1p(np.exp(-2.0 * z))
+    return (0.5 * (rho1 + rho2) * (1.0 - y)
+            + 0.5 * L * (rho2 - rho1) * (lncosh2(0.5 / L) - lncosh2((y - 0.5) / L)))
+
+
+def rayleigh_taylor_2d(n: int = 256, xi: float = 10.0, variant: str = "pvs", rho1: float = 1.0, rho2: float = 10.0,
+                       L: float = 0.025, amp: float = 0.01, pc: float = 1000.0, gy: float = -1.0,
+                       gamma: float = 5.0 / 3.0) -> Dict:
+    """[0,1]^2, periodic x, free-slip (reflecting) y walls, gravity (0, gy):
+    rho = {rho1 + (rho2 - rho1)/2 [1 + tanh((y - 1/2)/L)]} (1 + amp sin(4 pi x)),
+    P = pc - m_c(y) gy (hydrostatic for the unperturbed profile), V = 0.
+    The unperturbed profile is returned as the background (with wall ghosts)."""
+    h = 1.0 / n
+    x = _centres(n, 1.0)
+    y = _centres(n, 1.0)
+    prof = lambda yy: rho1 + 0.5 * (rho2 - rho1) * (1.0 + np.tanh((yy - 0.5) / L))
+    eps = amp * np.sin(4.0 * math.pi * x)
+    rho = prof(y)[:, None] * (1.0 + eps[None, :])
+    p = np.broadcast_to((pc - rt_column_mass(y, rho1, rho2, L) * gy)[:, None], rho.shape)
+    zero = np.zeros_like(rho)
+    yg = _centres(n + 4, (n + 4) * h, origin=-2.0 * h)
+    return _base(2, (n, n), (h, h), gamma, xi, variant, ("periodic", "reflect"), grav=(0.0, gy, 0.0), vertical=1,
+                 bg_rho=prof(yg), bg_p=pc - rt_column_mass(yg, rho1, rho2, L) * gy,
+                 U=_pack(rho, [zero, zero], p, gamma), name="rayleigh_taylor_2d")

@@ -58,6 +58,7 @@ def lib():
             "rsst_step": (i32, [vp, dbl, i32]),
             "rsst_dt": (i32, [vp, pd]),
             "rsst_sync": (i32, [vp]),
+            "rsst_time": (i32, [vp, pd]),
             "rsst_conserved_sums": (i32, [vp, pd]),
             "rsst_kernel_launches": (i64, [vp]),
             "rsst_conserved_sums_noalloc": (i32, [vp, i32, C.POINTER(C.c_int32), pd, vp, vp]),
@@ -170,6 +171,12 @@ def rsst_dt(h: int) -> float:
     return out.value
 
 
+def rsst_time(h: int) -> float:
+    t = C.c_double()
+    _check(lib().rsst_time(h, C.byref(t)), "rsst_time")
+    return t.value
+
+
 def rsst_sync(h: int) -> None:
     _check(lib().rsst_sync(h), "rsst_sync")
 
@@ -260,6 +267,9 @@ class Solver:
 
     def sync(self) -> None:
         rsst_sync(self.h)
+
+    def time(self) -> float:
+        return rsst_time(self.h)
 
     def sums(self) -> list:
         return rsst_conserved_sums(self.h, self.nvar)
