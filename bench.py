@@ -171,9 +171,10 @@ def workload(args):
 
 def bytes_per_cell_stage(w, precision):
     """Algorithmic HBM bytes per cell per stage: stage 1 reads and writes one
-    state, stage 2 reads two and writes one: 2.5 * nvar * bytes per scalar."""
+    state, stage 2 reads two and writes one: 2.5 * nvar * bytes per scalar
+    (8 for float64 and double-float, 4 for float32)."""
     nvar = w["ndim"] + 2
-    return 2.5 * nvar * (8 if precision == "fp64" else 4)
+    return 2.5 * nvar * (4 if precision == "fp32_pert" else 8)
 
 
 def _time_single(w, precision, steps, warmup, dev, flush_l2):
@@ -221,9 +222,16 @@ def run_modes(dev, peaks, sm_mhz):
     w = inputs.shear_layer_2d(2048, 2048, xi=30.0, variant="pvs")
     out["fp32_pert_shear_2048"] = _mode_line(w, "fp32_pert", _time_single(w, "fp32_pert", 20, 3, dev, False), 20, peaks,
                                              {"bound": "hbm (instruction-issue limited)"})
+    w = inputs.shear_layer_2d(512, 512, xi=30.0, variant="pvs")
+    out["fp64_df_shear_512"] = _mode_line(w, "fp64", _time_single(w, "fp64_df", 20, 3, dev, True), 20, peaks,
+                                          {"bound": "alu (float32 pipe, double-float arithmetic)",
+                                           "dtype": "f32x2 double-float (48-bit significand), parity 1e-10 vs f64"})
     w = inputs.polytrope_3d(variant="pvs")
     t = _time_single(w, "fp64", 5, 2, dev, False)
     out["fp64_polytrope_3d"] = _mode_line(w, "fp64", t, 5, peaks, {"bound": "alu (float64)"})
+    out["fp64_df_polytrope_3d"] = _mode_line(w, "fp64", _time_single(w, "fp64_df", 10, 2, dev, False), 10, peaks,
+                                             {"bound": "alu (float32 pipe, double-float arithmetic)",
+                                              "dtype": "f32x2 double-float (48-bit significand), parity 1e-10 vs f64"})
     out["fp32_pert_polytrope_3d"] = _mode_line(w, "fp32_pert", _time_single(w, "fp32_pert", 20, 3, dev, False), 20,
                                                peaks, {"bound": "hbm (instruction-issue limited)"})
     # adjoint: 2D 256^2 stratified box, 400 steps, checkpoint every 20
@@ -489,7 +497,7 @@ def main():
     ap.add_argument("--n", type=int, default=512)
     ap.add_argument("--variant", default="pvs")
     ap.add_argument("--workload", default="shear2d", choices=["shear2d", "polytrope3d", "batched"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32_pert"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32_pert", "fp64_df"])
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-modes", action="store_true", help="only the headline configuration")

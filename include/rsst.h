@@ -58,7 +58,11 @@ typedef enum {
 
 typedef enum {
   RSST_FP64 = 0,      /* state stored and computed in float64 */
-  RSST_FP32_PERT = 1  /* float32 perturbation about a float64 background */
+  RSST_FP32_PERT = 1, /* float32 perturbation about a float64 background */
+  RSST_FP64_DF = 2    /* double-float: state stored and computed as pairs of
+                       * float32 (hi + lo, 48-bit significand) on the float32
+                       * pipe; float64 results to ~1e-13 at a fraction of the
+                       * cost on GPUs with a slow float64 pipe */
 } rsst_precision;
 
 typedef enum { RSST_BC_PERIODIC = 0, RSST_BC_REFLECT = 1 } rsst_bc;

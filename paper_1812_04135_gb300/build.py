@@ -39,7 +39,8 @@ FP32_FLAGS = ["-prec-div=false", "-prec-sqrt=false"]
 
 def _compile(src: str, extra) -> str:
     obj = os.path.join(BUILD, os.path.basename(src) + ".o")
-    per_file = FP32_FLAGS if "fp32" in os.path.basename(src) or "batch" in os.path.basename(src) else []
+    base = os.path.basename(src)
+    per_file = FP32_FLAGS if ("fp32" in base or "batch" in base or "_df" in base) else []
     cmd = [nvcc(), *ARCH, *FLAGS, *per_file, *extra, "-c", src, "-o", obj]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:

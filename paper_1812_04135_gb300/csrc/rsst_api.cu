@@ -8,6 +8,8 @@
 
 #include <cudaTypedefs.h>
 
+#include <type_traits>
+
 #include "rsst_internal.h"
 
 static thread_local char g_err[512] = "";
@@ -95,7 +97,7 @@ static int validate(const rsst_config* c) {
     if (c->bc[d] != RSST_BC_PERIODIC && c->bc[d] != RSST_BC_REFLECT) { rsst_set_error("bc[%d] invalid", d); return RSST_EINVAL; }
   }
   if (c->variant < RSST_EULER || c->variant > RSST_PD) { rsst_set_error("variant %d invalid", c->variant); return RSST_EINVAL; }
-  if (c->precision != RSST_FP64 && c->precision != RSST_FP32_PERT) { rsst_set_error("precision %d invalid", c->precision); return RSST_EINVAL; }
+  if (c->precision != RSST_FP64 && c->precision != RSST_FP32_PERT && c->precision != RSST_FP64_DF) { rsst_set_error("precision %d invalid", c->precision); return RSST_EINVAL; }
   if (!(c->xi >= 1.0) || !std::isfinite(c->xi)) { rsst_set_error("xi must be finite and >= 1 (got %g)", c->xi); return RSST_EINVAL; }
   if (!(c->gamma > 1.0)) { rsst_set_error("gamma must be > 1"); return RSST_EINVAL; }
   if (!(c->cfl > 0.0)) { rsst_set_error("cfl must be > 0"); return RSST_EINVAL; }
@@ -189,7 +191,7 @@ extern "C" int rsst_init(rsst_handle** out, const rsst_config* cfg, void* stream
   h->cfg.bg_rho = nullptr;
   h->cfg.bg_p = nullptr;
   h->stream = (cudaStream_t)stream;
-  h->elem = cfg->precision == RSST_FP64 ? sizeof(double) : sizeof(float);
+  h->elem = cfg->precision == RSST_FP32_PERT ? sizeof(float) : sizeof(double);  // a double-float is 8 bytes
   make_geom(cfg, h->elem, &h->g);
   make_phys(cfg, &h->p);
   make_physf(&h->p, &h->pf);
@@ -286,14 +288,19 @@ extern "C" int rsst_set_state(rsst_handle* h, const double* U, int on_host) {
     src = h->d_stage;
   }
   const bool f32 = h->cfg.precision == RSST_FP32_PERT;
+  const bool dfp = h->cfg.precision == RSST_FP64_DF;
   if (f32)
     RC_TRY(rsst_launch_pack_fp32(src, (float*)h->buf[0], h->g, h->p, h->d_bg, h->bg_len, h->stream));
+  else if (dfp)
+    RC_TRY(rsst_launch_pack_df(src, (float2*)h->buf[0], h->g, h->p, h->d_bg, h->bg_len, h->stream));
   else
     RC_TRY(rsst_launch_pack_fp64(src, (double*)h->buf[0], h->g, h->p, h->d_bg, h->bg_len, h->stream));
   CUDA_TRY(cudaMemsetAsync(h->d_flag, 0, sizeof(unsigned int), h->stream));
   CUDA_TRY(cudaMemsetAsync(h->d_scal + h->slot, 0, sizeof(double), h->stream));
   CUDA_TRY(cudaMemsetAsync(h->d_scal + 3, 0, sizeof(double), h->stream));  // simulated time
-  if (f32)
+  if (dfp)
+    RC_TRY(rsst_launch_cfl_df((const float2*)h->buf[0], h->g, h->p, h->d_scal + h->slot, h->d_flag, h->stream));
+  else if (f32)
     RC_TRY(rsst_launch_cfl_fp32((const float*)h->buf[0], h->g, h->p, h->pf, h->d_tab, h->bg_len, h->d_scal + h->slot,
                                 h->d_flag, h->stream));
   else
@@ -309,6 +316,8 @@ extern "C" int rsst_get_state(rsst_handle* h, double* U, int on_host) {
   double* dst = on_host ? h->d_stage : U;
   if (h->cfg.precision == RSST_FP32_PERT)
     RC_TRY(rsst_launch_unpack_fp32((const float*)h->buf[0], dst, h->g, h->p, h->d_bg, h->bg_len, h->stream));
+  else if (h->cfg.precision == RSST_FP64_DF)
+    RC_TRY(rsst_launch_unpack_df((const float2*)h->buf[0], dst, h->g, h->stream));
   else
     RC_TRY(rsst_launch_unpack_fp64((const double*)h->buf[0], dst, h->g, h->stream));
   h->launches += 1;
@@ -338,7 +347,8 @@ static int run_steps(rsst_handle* h, double dt, int nsteps) {
     a.in = U;
     a.base = nullptr;
     a.out = Us;
-    if constexpr (sizeof(T) == 8) RC_TRY(rsst_launch_stage_fp64(a, h->stream));
+    if constexpr (std::is_same<T, double>::value) RC_TRY(rsst_launch_stage_fp64(a, h->stream));
+    else if constexpr (std::is_same<T, float2>::value) RC_TRY(rsst_launch_stage_df(a, h->stream));
     else if (h->use_tma2d) RC_TRY(rsst_launch_stage2d_tma(&h->tmap[0], a, h->stream));
     else if (h->use_tma3d) RC_TRY(rsst_launch_stage3d_tma(&h->tmap[0], a, h->stream));
     else RC_TRY(rsst_launch_stage_fp32(a, h->stream));
@@ -346,7 +356,8 @@ static int run_steps(rsst_handle* h, double dt, int nsteps) {
     a.in = Us;
     a.base = U;
     a.out = U;
-    if constexpr (sizeof(T) == 8) RC_TRY(rsst_launch_stage_fp64(a, h->stream));
+    if constexpr (std::is_same<T, double>::value) RC_TRY(rsst_launch_stage_fp64(a, h->stream));
+    else if constexpr (std::is_same<T, float2>::value) RC_TRY(rsst_launch_stage_df(a, h->stream));
     else if (h->use_tma2d) RC_TRY(rsst_launch_stage2d_tma(&h->tmap[1], a, h->stream));
     else if (h->use_tma3d) RC_TRY(rsst_launch_stage3d_tma(&h->tmap[1], a, h->stream));
     else RC_TRY(rsst_launch_stage_fp32(a, h->stream));
@@ -358,6 +369,7 @@ static int run_steps(rsst_handle* h, double dt, int nsteps) {
 
 int rsst_handle_steps(rsst_handle* h, double dt, int nsteps) {
   if (h->cfg.precision == RSST_FP32_PERT) return run_steps<float>(h, dt, nsteps);
+  if (h->cfg.precision == RSST_FP64_DF) return run_steps<float2>(h, dt, nsteps);
   return run_steps<double>(h, dt, nsteps);
 }
 
@@ -398,6 +410,8 @@ extern "C" int rsst_conserved_sums(rsst_handle* h, double* sums) {
   if (h->cfg.precision == RSST_FP32_PERT)
     RC_TRY(rsst_launch_sums_fp32((const float*)h->buf[0], h->g, h->p, h->d_bg, h->bg_len, h->d_partial, h->d_scal + 8,
                                  vol, h->stream));
+  else if (h->cfg.precision == RSST_FP64_DF)
+    RC_TRY(rsst_launch_sums_df((const float2*)h->buf[0], h->g, h->d_partial, h->d_scal + 8, vol, h->stream));
   else
     RC_TRY(rsst_launch_sums_fp64((const double*)h->buf[0], h->g, h->d_partial, h->d_scal + 8, vol, h->stream));
   h->launches += 2;

@@ -102,6 +102,13 @@ int rsst_launch_sums_fp64(const double* U, const Geom& g, double* partial, doubl
                           double scale, cudaStream_t s);
 
 int rsst_launch_stage_fp32(const StageArgs<float>& a, cudaStream_t s);
+int rsst_launch_stage_df(const StageArgs<float2>& a, cudaStream_t s);
+int rsst_launch_pack_df(const double* src, float2* dst, const Geom& g, const Phys& p, const double* bg, int bg_len,
+                        cudaStream_t s);
+int rsst_launch_unpack_df(const float2* src, double* dst, const Geom& g, cudaStream_t s);
+int rsst_launch_cfl_df(const float2* U, const Geom& g, const Phys& p, double* slot_ptr, unsigned int* flag,
+                       cudaStream_t s);
+int rsst_launch_sums_df(const float2* U, const Geom& g, double* partial, double* out, double scale_, cudaStream_t s);
 int rsst_launch_stage2d_tma(const CUtensorMap* tin, const StageArgs<float>& a, cudaStream_t s);
 int rsst_launch_stage3d_tma(const CUtensorMap* tin, const StageArgs<float>& a, cudaStream_t s);
 int rsst_launch_bgtab(const double* bg, int bg_len, const Geom& g, const Phys& p, float* tab, cudaStream_t s);

@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_PKG, "librsst.so")
 RSST_OK, RSST_EINVAL, RSST_ECUDA, RSST_ENONPHYSICAL, RSST_ETIMEOUT, RSST_EUNSUPPORTED, RSST_ENOMEM = 0, -1, -2, -3, -4, -5, -6
 ERROR_NAMES = {-1: "EINVAL", -2: "ECUDA", -3: "ENONPHYSICAL", -4: "ETIMEOUT", -5: "EUNSUPPORTED", -6: "ENOMEM"}
 VARIANTS = {"euler": 0, "dvs": 1, "pvs": 2, "dms": 3, "pms": 4, "pd": 5}
-PRECISIONS = {"fp64": 0, "fp32_pert": 1}
+PRECISIONS = {"fp64": 0, "fp32_pert": 1, "fp64_df": 2}
 BCS = {"periodic": 0, "reflect": 1}
 
 
