@@ -98,18 +98,52 @@ class Problem:
 
 
 # ---------------------------------------------------------------------------
-# Primitive variables (Sec. 2.1, Sec. 3.2: E = e + rho V^2/2, e = P/(gamma-1),
-# a^2 = gamma P / rho)
+# Equation of state (Sec. 3.2: the equations hold for a general EOS P(rho, S);
+# Eq. pvs_cons_therm gives the derivatives the pressure tendency needs)
 # ---------------------------------------------------------------------------
 
-def primitives(U: torch.Tensor, gamma: float):
-    """Return rho, list of V_d, |V|^2, P, a^2 of a conservative state."""
+class IdealGas:
+    """e = P/(gamma-1) (e: internal energy per volume), a^2 = gamma P/rho,
+    (de/dP)_rho = 1/(gamma-1), (de/drho)_P = 0 (Sec. 3.2)."""
+
+    def __init__(self, gamma: float):
+        self.gamma = float(gamma)
+
+    def pressure(self, rho, eint):
+        return (self.gamma - 1.0) * eint
+
+    def internal_energy(self, rho, P):
+        return P / (self.gamma - 1.0)
+
+    def sound2(self, rho, P):
+        return self.gamma * P / rho
+
+    def de_dP(self, rho, P):
+        return 1.0 / (self.gamma - 1.0) + 0.0 * P
+
+    def de_drho(self, rho, P):
+        return 0.0 * P
+
+
+def as_eos(g):
+    """An EOS object, or the ideal gas of ratio g."""
+    return g if hasattr(g, "pressure") else IdealGas(g)
+
+
+# ---------------------------------------------------------------------------
+# Primitive variables (Sec. 2.1, Sec. 3.2: E = e + rho V^2/2)
+# ---------------------------------------------------------------------------
+
+def primitives(U: torch.Tensor, gamma):
+    """Return rho, list of V_d, |V|^2, P, a^2 of a conservative state
+    (``gamma``: the ideal-gas ratio or an EOS object)."""
+    eos = as_eos(gamma)
     nd = U.shape[0] - 2
     rho = U[0]
     V = [U[1 + d] / rho for d in range(nd)]
     v2 = sum(v * v for v in V)
-    P = (gamma - 1.0) * (U[-1] - 0.5 * rho * v2)
-    a2 = gamma * P / rho
+    P = eos.pressure(rho, U[-1] - 0.5 * rho * v2)
+    a2 = eos.sound2(rho, P)
     return rho, V, v2, P, a2
 
 
@@ -178,7 +212,7 @@ def _background_state(prob: Problem, k_lo: int, count: int) -> Optional[torch.Te
     if prob.bg_rho is None:
         return None
     rho0 = prob.bg_rho[k_lo:k_lo + count].to(DT)
-    e0 = prob.bg_p[k_lo:k_lo + count].to(DT) / (prob.gamma - 1.0)
+    e0 = as_eos(prob.gamma).internal_energy(rho0, prob.bg_p[k_lo:k_lo + count].to(DT))
     comps = [rho0] + [torch.zeros_like(rho0)] * prob.ndim + [e0]
     return torch.stack(comps)  # [nvar, count]
 
@@ -244,12 +278,13 @@ def euler_tendency(U: torch.Tensor, prob: Problem) -> torch.Tensor:
 # RSST correction (Sec. 3.2 Eqs. pvs_dt / pvs_dt_dpr / pvs_cons_rhs; App. A)
 # ---------------------------------------------------------------------------
 
-def pressure_tendency(U: torch.Tensor, dU: torch.Tensor, gamma: float) -> torch.Tensor:
-    """dP = [(de/dP)_rho]^-1 {[V^2/2 - (de/drho)_P] drho - V.dm + dE}, ideal gas (Eq. pvs_dt_dpr)."""
-    rho, V, v2, P, a2 = primitives(U, gamma)
+def pressure_tendency(U: torch.Tensor, dU: torch.Tensor, gamma) -> torch.Tensor:
+    """dP = [(de/dP)_rho]^-1 {[V^2/2 - (de/drho)_P] drho - V.dm + dE} (Eq. pvs_dt_dpr)."""
+    eos = as_eos(gamma)
+    rho, V, v2, P, a2 = primitives(U, eos)
     nd = U.shape[0] - 2
     vdm = sum(V[e] * dU[1 + e] for e in range(nd))
-    return (gamma - 1.0) * (0.5 * v2 * dU[0] - vdm + dU[-1])
+    return ((0.5 * v2 - eos.de_drho(rho, P)) * dU[0] - vdm + dU[-1]) / eos.de_dP(rho, P)
 
 
 def correction_vector(U: torch.Tensor, variant: int, gamma: float):
@@ -261,9 +296,10 @@ def correction_vector(U: torch.Tensor, variant: int, gamma: float):
     DMS: r = (1, 0, (e+P-rho V^2/2)/rho)                 App. A.3
     PD : r = (0, 0, (de/dP)_rho = 1/(gamma-1))           App. A.4
     """
-    rho, V, v2, P, a2 = primitives(U, gamma)
+    eos = as_eos(gamma)
+    rho, V, v2, P, a2 = primitives(U, eos)
     nd = U.shape[0] - 2
-    e = P / (gamma - 1.0)
+    e = eos.internal_energy(rho, P)
     one = torch.ones_like(rho)
     zero = torch.zeros_like(rho)
     if variant == PVS:
@@ -275,7 +311,7 @@ def correction_vector(U: torch.Tensor, variant: int, gamma: float):
     if variant == DMS:
         return "rho", [one] + [zero] * nd + [(e + P - 0.5 * rho * v2) / rho]
     if variant == PD:
-        return "P", [zero] * (nd + 1) + [one / (gamma - 1.0)]
+        return "P", [zero] * (nd + 1) + [eos.de_dP(rho, P) * one]
     raise ValueError(f"no correction vector for variant {variant}")
 
 

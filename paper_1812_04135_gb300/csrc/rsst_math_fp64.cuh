@@ -8,6 +8,29 @@
 
 namespace rsst {
 
+// Equation-of-state hook (Sec. 3.2: the reduced equations hold for a general
+// EOS; the pressure tendency needs (de/dP)_rho and (de/drho)_P, Eqs.
+// pvs_cons_dpr / pvs_cons_therm).  The float64 step reads its thermodynamics
+// only through these members; this build compiles the ideal gas
+// (e = P/(gamma-1), the only EOS the paper specifies).  Another EOS is a
+// struct with the same members selected by `Eos` below.
+struct IdealGasEos {
+  // P from the total energy E and rho |V|^2
+  __device__ static __forceinline__ double pressure(const Phys& p, double rho, double E, double rhov2) {
+    return p.gm1 * E - p.hgm1 * rhov2;
+  }
+  __device__ static __forceinline__ double sound2(const Phys& p, double rho, double P, double inv_rho) {
+    return p.gamma * P * inv_rho;
+  }
+  __device__ static __forceinline__ double internal_energy(const Phys& p, double rho, double P) {
+    return P * p.inv_gm1;
+  }
+  __device__ static __forceinline__ double de_dP(const Phys& p, double rho, double P) { return p.inv_gm1; }
+  __device__ static __forceinline__ double inv_de_dP(const Phys& p, double rho, double P) { return p.gm1; }
+  __device__ static __forceinline__ double de_drho(const Phys& p, double rho, double P) { return 0.0; }
+};
+using Eos = IdealGasEos;
+
 // 1/x to full float64 accuracy with few float64-pipe instructions: the
 // hardware reciprocal approximation followed by two Newton-Raphson steps
 // y <- y + y (1 - x y) (each doubles the number of correct bits).  Within an
@@ -49,8 +72,8 @@ __device__ __forceinline__ void euler_flux(const double (&q)[NV], const Phys& p,
     v[e] = q[1 + e] * ir;
     v2 += v[e] * v[e];
   }
-  const double P = p.gm1 * q[NV - 1] - p.hgm1 * (rho * v2);
-  c = sqrt(v2) + sound_over_xi(p.gamma * P * ir, p);
+  const double P = Eos::pressure(p, rho, q[NV - 1], rho * v2);
+  c = sqrt(v2) + sound_over_xi(Eos::sound2(p, rho, P, ir), p);
   // half fluxes: the LLF average of the two sides needs F/2
   const double hv = 0.5 * v[D];
   F[0] = 0.5 * q[1 + D];
@@ -115,17 +138,17 @@ __device__ __forceinline__ void rsst_rhs(const double (&q)[NV], double (&dU)[NV]
       v2 += v[e] * v[e];
       vdm += v[e] * dU[1 + e];
     }
-    const double P = p.gm1 * (q[NV - 1] - 0.5 * rho * v2);
-    const double e_int = P * p.inv_gm1;
+    const double P = Eos::pressure(p, rho, q[NV - 1], rho * v2);
+    const double e_int = Eos::internal_energy(p, rho, P);
     const double kin = 0.5 * rho * v2;
     double s, r0, rv, rE;  // r = (r0, rv * V, rE); rv in {0, 1/a^2, 1}
     const int var = p.variant;
     if (var == RSST_PVS || var == RSST_PMS || var == RSST_PD) {
-      s = p.gm1 * (0.5 * v2 * dU[0] - vdm + dU[NV - 1]);
+      s = Eos::inv_de_dP(p, rho, P) * ((0.5 * v2 - Eos::de_drho(p, rho, P)) * dU[0] - vdm + dU[NV - 1]);
       if (var == RSST_PD) {
-        r0 = 0.0; rv = 0.0; rE = p.inv_gm1;
+        r0 = 0.0; rv = 0.0; rE = Eos::de_dP(p, rho, P);
       } else {
-        const double ia2 = rho * rcp_nr(p.gamma * P);  // 1/a^2
+        const double ia2 = rcp_nr(Eos::sound2(p, rho, P, ir));  // 1/a^2
         r0 = ia2;
         rv = (var == RSST_PVS) ? ia2 : 0.0;
         rE = (var == RSST_PVS ? (e_int + P + kin) : (e_int + P - kin)) * ia2 * ir;
@@ -136,7 +159,7 @@ __device__ __forceinline__ void rsst_rhs(const double (&q)[NV], double (&dU)[NV]
       rv = (var == RSST_DVS) ? 1.0 : 0.0;
       rE = (var == RSST_DVS ? (e_int + P + kin) : (e_int + P - kin)) * ir;
     }
-    const double fs = f_of(p.gamma * P * ir, p) * s;
+    const double fs = f_of(Eos::sound2(p, rho, P, ir), p) * s;
     dU[0] -= fs * r0;
 #pragma unroll
     for (int e = 0; e < ND; ++e) dU[1 + e] -= fs * (rv * v[e]);
@@ -167,9 +190,9 @@ __device__ __forceinline__ double cfl_rate(const double (&q)[NV], const Phys& p,
     v2 += ve * ve;
     fin = fin && isfinite(q[1 + e]);
   }
-  const double P = p.gm1 * (q[NV - 1] - 0.5 * rho * v2);
+  const double P = Eos::pressure(p, rho, q[NV - 1], rho * v2);
   ok = fin && rho > 0.0 && P > 0.0;
-  const double c = sqrt(v2) + sound_over_xi(p.gamma * P * ir, p);
+  const double c = sqrt(v2) + sound_over_xi(Eos::sound2(p, rho, P, ir), p);
   return c * p.sum_inv_dx;
 }
 
