@@ -472,7 +472,8 @@ def run_gpu(args, world, rank, local):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_max / args.steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64" if args.precision == "fp64" else "f32 (perturbation about an f64 background)",
+            "dtype": {"fp64": "f64", "fp32_pert": "f32 (perturbation about an f64 background)",
+                      "fp64_df": "f32x2 double-float (48-bit significand)"}[args.precision],
             "data": "synthetic", "config": _config(args, w),
             "roofline": roof,
             "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},

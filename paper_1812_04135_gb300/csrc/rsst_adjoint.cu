@@ -19,8 +19,10 @@
 //     contributions of the faces whose stencil holds it;
 //   adj_fold: ghost-cell adjoints go back to the cells they were copied from
 //     (wrap, or mirror with the normal momentum negated).
-// The derivatives are taken with a forward-mode dual number run once per
-// input component over templated copies of the step's arithmetic.
+// The derivatives are hand-derived reverse mode: each VJP recomputes its
+// forward values (holding the branches the forward pass took) and then runs
+// the chain rule backwards once, so a face costs about three flux
+// evaluations whatever the size of its stencil.
 #include <cstring>
 #include <vector>
 
@@ -29,143 +31,279 @@
 
 namespace rsst {
 
-struct Dual {
-  double v, d;
-};
-__device__ __forceinline__ Dual mk(double v, double d = 0.0) { return {v, d}; }
-__device__ __forceinline__ Dual operator+(Dual a, Dual b) { return {a.v + b.v, a.d + b.d}; }
-__device__ __forceinline__ Dual operator-(Dual a, Dual b) { return {a.v - b.v, a.d - b.d}; }
-__device__ __forceinline__ Dual operator-(Dual a) { return {-a.v, -a.d}; }
-__device__ __forceinline__ Dual operator+(Dual a, double b) { return {a.v + b, a.d}; }
-__device__ __forceinline__ Dual operator+(double a, Dual b) { return {a + b.v, b.d}; }
-__device__ __forceinline__ Dual operator-(Dual a, double b) { return {a.v - b, a.d}; }
-__device__ __forceinline__ Dual operator-(double a, Dual b) { return {a - b.v, -b.d}; }
-__device__ __forceinline__ Dual operator*(Dual a, Dual b) { return {a.v * b.v, a.d * b.v + a.v * b.d}; }
-__device__ __forceinline__ Dual operator*(double a, Dual b) { return {a * b.v, a * b.d}; }
-__device__ __forceinline__ Dual operator*(Dual a, double b) { return {a.v * b, a.d * b}; }
-__device__ __forceinline__ Dual operator/(Dual a, Dual b) {
-  const double q = a.v / b.v;
-  return {q, (a.d - q * b.d) / b.v};
-}
-__device__ __forceinline__ Dual operator/(double a, Dual b) {
-  const double q = a / b.v;
-  return {q, -q * b.d / b.v};
-}
-__device__ __forceinline__ Dual dsqrt(Dual a) {
-  const double s = sqrt(a.v);
-  return {s, a.v > 0.0 ? a.d / (2.0 * s) : 0.0};
-}
-__device__ __forceinline__ double val(double a) { return a; }
-__device__ __forceinline__ double val(Dual a) { return a.v; }
-__device__ __forceinline__ double dsqrt(double a) { return sqrt(a); }
-
 // |V| with a zero subgradient at V = 0.
-template <class T>
-__device__ __forceinline__ T speed_T(T v2) {
-  if (val(v2) > 0.0) return dsqrt(v2);
-  return v2 * 0.0;
+__device__ __forceinline__ double speed_of(double v2) { return v2 > 0.0 ? sqrt(v2) : 0.0; }
+
+// MC branch (Sec. 4.2): 0 -> 0, 1 -> 2a, 2 -> 2b, 3 -> (a+b)/2; the
+// comparisons are the oracle's, so ties take the same branch.
+__device__ __forceinline__ int mc_branch(double a, double b) {
+  if (!(a * b > 0.0)) return 0;
+  const double aa = 2.0 * fabs(a), bb = 2.0 * fabs(b), cc = 0.5 * fabs(a + b);
+  if (aa <= bb && aa <= cc) return 1;
+  return bb <= cc ? 2 : 3;
+}
+__device__ __forceinline__ double mc_value(int br, double a, double b) {
+  return br == 0 ? 0.0 : (br == 1 ? 2.0 * a : (br == 2 ? 2.0 * b : 0.5 * (a + b)));
+}
+// d(slope)/da and d(slope)/db of the taken branch, times the slope's adjoint ds.
+__device__ __forceinline__ void mc_reverse(int br, double ds, double& da, double& db) {
+  da = br == 1 ? 2.0 * ds : (br == 3 ? 0.5 * ds : 0.0);
+  db = br == 2 ? 2.0 * ds : (br == 3 ? 0.5 * ds : 0.0);
 }
 
-template <class T>
-__device__ __forceinline__ T mc_T(T a, T b) {
-  const double av = val(a), bv = val(b);
-  if (!(av * bv > 0.0)) return a * 0.0;
-  const double aa = 2.0 * fabs(av), bb = 2.0 * fabs(bv), cc = 0.5 * fabs(av + bv);
-  if (aa <= bb && aa <= cc) return 2.0 * a;
-  if (bb <= cc) return 2.0 * b;
-  return 0.5 * (a + b);
+// a/xi of a state (constant xi, or the C_max law, Eq. cx).
+__device__ __forceinline__ double sound_term(double a2, const Phys& p) {
+  if (p.use_cmax) return sqrt(a2 / sqrt(1.0 + (a2 * a2) * p.inv_cmax4));
+  return sqrt(a2) * p.inv_xi;
 }
 
-template <class T, int NV, int D>
-__device__ __forceinline__ void euler_flux_T(const T (&q)[NV], const Phys& p, T inv_xi, T (&F)[NV], T& c) {
+// Euler flux along D and c_tot = |V| + a/xi of one state (Sec. 4.2).
+template <int NV, int D>
+__device__ __forceinline__ void euler_flux_d(const double (&q)[NV], const Phys& p, double (&F)[NV], double& c) {
   constexpr int ND = NV - 2;
-  const T rho = q[0];
-  T v[ND];
-  T v2 = q[0] * 0.0;
+  const double rho = q[0];
+  double v[ND];
+  double v2 = 0.0;
   for (int e = 0; e < ND; ++e) {
     v[e] = q[1 + e] / rho;
-    v2 = v2 + v[e] * v[e];
+    v2 += v[e] * v[e];
   }
-  const T P = p.gm1 * (q[NV - 1] - 0.5 * (rho * v2));
-  const T a2 = p.gamma * P / rho;
-  if (p.use_cmax)  // C_max law (Eq. cx): a/xi = sqrt(a^2 / sqrt(1 + a^4/C^4))
-    c = speed_T(v2) + dsqrt(a2 / dsqrt(1.0 + (a2 * a2) * p.inv_cmax4));
-  else
-    c = speed_T(v2) + dsqrt(a2) * inv_xi;
+  const double P = p.gm1 * (q[NV - 1] - 0.5 * (rho * v2));
+  c = speed_of(v2) + sound_term(p.gamma * P / rho, p);
   F[0] = q[1 + D];
   for (int e = 0; e < ND; ++e) F[1 + e] = (e == D) ? q[1 + e] * v[D] + P : q[1 + e] * v[D];
   F[NV - 1] = (q[NV - 1] + P) * v[D];
 }
 
-// LLF flux of the face between cells u0 | u1 from the stencil (um, u0 | u1, up).
-template <class T, int NV, int D>
-__device__ __forceinline__ void face_T(const T (&um)[NV], const T (&u0)[NV], const T (&u1)[NV], const T (&up)[NV],
-                                       const Phys& p, T inv_xi, T (&F)[NV]) {
-  T qL[NV], qR[NV], FL[NV], FR[NV], cL, cR;
+// Face states of the face between u0 | u1 from the stencil (um, u0 | u1, up):
+// MUSCL-MC reconstruction, with the branches taken.
+template <int NV>
+__device__ __forceinline__ void face_states(const double (&s)[4][NV], double (&qL)[NV], double (&qR)[NV],
+                                            int (&bL)[NV], int (&bR)[NV]) {
   for (int v = 0; v < NV; ++v) {
-    qL[v] = u0[v] + 0.5 * mc_T(u0[v] - um[v], u1[v] - u0[v]);
-    qR[v] = u1[v] - 0.5 * mc_T(u1[v] - u0[v], up[v] - u1[v]);
+    const double aL = s[1][v] - s[0][v], dL = s[2][v] - s[1][v];
+    const double aR = s[2][v] - s[1][v], dR = s[3][v] - s[2][v];
+    bL[v] = mc_branch(aL, dL);
+    bR[v] = mc_branch(aR, dR);
+    qL[v] = s[1][v] + 0.5 * mc_value(bL[v], aL, dL);
+    qR[v] = s[2][v] - 0.5 * mc_value(bR[v], aR, dR);
   }
-  euler_flux_T<T, NV, D>(qL, p, inv_xi, FL, cL);
-  euler_flux_T<T, NV, D>(qR, p, inv_xi, FR, cR);
-  const T alpha = val(cL) >= val(cR) ? cL : cR;
+}
+
+// LLF flux F = (FL + FR)/2 - alpha (qR - qL)/2, alpha = max(cL, cR) with ties
+// to the left state (Sec. 4.2).
+template <int NV, int D>
+__device__ __forceinline__ void face_flux(const double (&s)[4][NV], const Phys& p, double (&F)[NV]) {
+  double qL[NV], qR[NV], FL[NV], FR[NV], cL, cR;
+  int bL[NV], bR[NV];
+  face_states<NV>(s, qL, qR, bL, bR);
+  euler_flux_d<NV, D>(qL, p, FL, cL);
+  euler_flux_d<NV, D>(qR, p, FR, cR);
+  const double alpha = cL >= cR ? cL : cR;
   for (int v = 0; v < NV; ++v) F[v] = 0.5 * (FL[v] + FR[v]) - 0.5 * (alpha * (qR[v] - qL[v]));
 }
 
-// Reduced tendency plus force at one cell: L = dU - f s r + (0, rho F, m.F).
-template <class T, int NV>
-__device__ __forceinline__ void rhs_T(const T (&q)[NV], const T (&dU)[NV], T f, const Phys& p, T (&L)[NV]) {
+// Reverse of euler_flux_d at q: adds dF^T dF/dq + dc dc/dq to dq and returns
+// dF^T dF/d(1/xi) + dc dc/d(1/xi).  Hand-derived chain rule through
+// v = m/rho, P = (gamma-1)(E - rho|v|^2/2), a^2 = gamma P/rho.
+template <int NV, int D>
+__device__ __forceinline__ double flux_vjp(const double (&q)[NV], const Phys& p, const double (&dF)[NV], double dc,
+                                           double (&dq)[NV]) {
   constexpr int ND = NV - 2;
-  for (int v = 0; v < NV; ++v) L[v] = dU[v];
-  const T rho = q[0];
-  if (p.variant != RSST_EULER) {
-    T v[ND];
-    T v2 = q[0] * 0.0, vdm = q[0] * 0.0;
+  const double rho = q[0], E = q[NV - 1];
+  double v[ND], dv[ND];
+  double v2 = 0.0;
+  for (int e = 0; e < ND; ++e) {
+    v[e] = q[1 + e] / rho;
+    v2 += v[e] * v[e];
+    dv[e] = 0.0;
+  }
+  const double P = p.gm1 * (E - 0.5 * (rho * v2));
+  const double a2 = p.gamma * P / rho;
+  double dP = dF[1 + D] + dF[NV - 1] * v[D], dv2 = 0.0, drho = 0.0, dE = dF[NV - 1] * v[D], dinv_xi = 0.0;
+  dq[1 + D] += dF[0];
+  for (int e = 0; e < ND; ++e) {
+    dq[1 + e] += dF[1 + e] * v[D];
+    dv[D] += dF[1 + e] * q[1 + e];
+  }
+  dv[D] += dF[NV - 1] * (E + P);
+  if (v2 > 0.0) dv2 += dc * 0.5 / sqrt(v2);
+  double da2 = 0.0;
+  if (p.use_cmax) {  // g = sqrt(u), u = a2 / t, t = sqrt(w), w = 1 + a2^2 / C^4
+    const double w = 1.0 + (a2 * a2) * p.inv_cmax4, t = sqrt(w), u = a2 / t;
+    if (u > 0.0) {
+      const double du = dc / (2.0 * sqrt(u));
+      const double dt = -du * u / t;
+      da2 += du / t + (dt / (2.0 * t)) * 2.0 * a2 * p.inv_cmax4;
+    }
+  } else {
+    const double s = sqrt(a2);
+    dinv_xi += dc * s;
+    if (a2 > 0.0) da2 += dc * p.inv_xi / (2.0 * s);
+  }
+  dP += da2 * p.gamma / rho;
+  drho -= da2 * a2 / rho;
+  dE += dP * p.gm1;
+  drho -= dP * p.gm1 * 0.5 * v2;
+  dv2 -= dP * p.gm1 * 0.5 * rho;
+  for (int e = 0; e < ND; ++e) {
+    dv[e] += 2.0 * v[e] * dv2;
+    dq[1 + e] += dv[e] / rho;
+    drho -= dv[e] * v[e] / rho;
+  }
+  dq[0] += drho;
+  dq[NV - 1] += dE;
+  return dinv_xi;
+}
+
+// Reverse of face_flux: G[k] = phi^T dF/d(stencil cell k), and the return
+// value phi^T dF/d(1/xi).  The forward branches (MC branch, LLF side) are
+// recomputed and held.
+template <int NV, int D>
+__device__ __forceinline__ double face_vjp(const double (&s)[4][NV], const double (&phi)[NV], const Phys& p,
+                                           double (&G)[4][NV]) {
+  double qL[NV], qR[NV], FL[NV], FR[NV], cL, cR;
+  int bL[NV], bR[NV];
+  face_states<NV>(s, qL, qR, bL, bR);
+  euler_flux_d<NV, D>(qL, p, FL, cL);
+  euler_flux_d<NV, D>(qR, p, FR, cR);
+  const bool left = cL >= cR;
+  const double alpha = left ? cL : cR;
+  double dF[NV], dqL[NV], dqR[NV], dalpha = 0.0;
+  for (int v = 0; v < NV; ++v) {
+    dF[v] = 0.5 * phi[v];
+    dqL[v] = 0.5 * alpha * phi[v];
+    dqR[v] = -0.5 * alpha * phi[v];
+    dalpha -= 0.5 * phi[v] * (qR[v] - qL[v]);
+  }
+  double dinv_xi = flux_vjp<NV, D>(qL, p, dF, left ? dalpha : 0.0, dqL);
+  dinv_xi += flux_vjp<NV, D>(qR, p, dF, left ? 0.0 : dalpha, dqR);
+  for (int v = 0; v < NV; ++v) {
+    double da, db;
+    // qL = u0 + MC(u0 - um, u1 - u0)/2
+    mc_reverse(bL[v], 0.5 * dqL[v], da, db);
+    G[0][v] = -da;
+    G[1][v] = dqL[v] + da - db;
+    G[2][v] = db;
+    // qR = u1 - MC(u1 - u0, up - u1)/2
+    mc_reverse(bR[v], -0.5 * dqR[v], da, db);
+    G[1][v] -= da;
+    G[2][v] += dqR[v] + da - db;
+    G[3][v] = db;
+  }
+  return dinv_xi;
+}
+
+// Reverse of the reduced tendency plus force at one cell,
+//   L = dU - f s r + (0, rho F, m.F)   (Sec. 3.2, App. A, App. B),
+// for the cotangent mu: nu = mu^T dL/d(dU), dq = mu^T dL/dq, and the return
+// value mu^T dL/df (zero under the C_max law, where f comes from the state).
+// With w = mu . r the correction contributes -f s w, so ds = -f w, dw = -f s.
+template <int NV>
+__device__ __forceinline__ double rhs_vjp(const double (&q)[NV], const double (&dU)[NV], const double (&mu)[NV],
+                                          const Phys& p, double (&nu)[NV], double (&dq)[NV]) {
+  constexpr int ND = NV - 2;
+  const double rho = q[0];
+  double dfc_total = 0.0;
+  for (int v = 0; v < NV; ++v) {
+    nu[v] = mu[v];
+    dq[v] = 0.0;
+  }
+  const int var = p.variant;
+  if (var != RSST_EULER) {
+    double v[ND], dv[ND];
+    double v2 = 0.0, vdm = 0.0, mv = 0.0;
     for (int e = 0; e < ND; ++e) {
       v[e] = q[1 + e] / rho;
-      v2 = v2 + v[e] * v[e];
-      vdm = vdm + v[e] * dU[1 + e];
+      v2 += v[e] * v[e];
+      vdm += v[e] * dU[1 + e];
+      mv += mu[1 + e] * v[e];
+      dv[e] = 0.0;
     }
-    const T P = p.gm1 * (q[NV - 1] - 0.5 * (rho * v2));
-    const T e_int = P * p.inv_gm1;
-    const T kin = 0.5 * (rho * v2);
-    const int var = p.variant;
-    T s, r0, rE;
-    T rv = q[0] * 0.0;
-    bool has_rv = false;
-    if (var == RSST_PVS || var == RSST_PMS || var == RSST_PD) {
+    const double E = q[NV - 1];
+    const double P = p.gm1 * (E - 0.5 * (rho * v2));
+    const double kin = 0.5 * (rho * v2);
+    const bool pform = var == RSST_PVS || var == RSST_PMS || var == RSST_PD;
+    const double sgn = (var == RSST_PVS || var == RSST_DVS) ? 1.0 : -1.0;
+    const double H = P * p.inv_gm1 + P + sgn * kin;  // e + P +- rho|V|^2/2
+    double s, r0, rv, rE, ia2 = 0.0;
+    if (pform) {
       s = p.gm1 * (0.5 * (v2 * dU[0]) - vdm + dU[NV - 1]);
       if (var == RSST_PD) {
-        r0 = q[0] * 0.0;
-        rE = q[0] * 0.0 + p.inv_gm1;
+        r0 = 0.0; rv = 0.0; rE = p.inv_gm1;
       } else {
-        const T ia2 = rho / (p.gamma * P);
+        ia2 = rho / (p.gamma * P);
         r0 = ia2;
-        if (var == RSST_PVS) { rv = ia2; has_rv = true; }
-        rE = (var == RSST_PVS ? (e_int + P + kin) : (e_int + P - kin)) * ia2 / rho;
+        rv = var == RSST_PVS ? ia2 : 0.0;
+        rE = H * ia2 / rho;
       }
     } else {
       s = dU[0];
-      r0 = q[0] * 0.0 + 1.0;
-      if (var == RSST_DVS) { rv = q[0] * 0.0 + 1.0; has_rv = true; }
-      rE = (var == RSST_DVS ? (e_int + P + kin) : (e_int + P - kin)) / rho;
+      r0 = 1.0;
+      rv = var == RSST_DVS ? 1.0 : 0.0;
+      rE = H / rho;
     }
-    // f = 1 - 1/xi^2: constant, or from the cell's a^2 under the C_max law
-    const T fc = p.use_cmax ? 1.0 - 1.0 / dsqrt(1.0 + ((p.gamma * P / rho) * (p.gamma * P / rho)) * p.inv_cmax4) : f;
-    const T fs = fc * s;
-    L[0] = L[0] - fs * r0;
-    if (has_rv)
-      for (int e = 0; e < ND; ++e) L[1 + e] = L[1 + e] - fs * (rv * v[e]);
-    L[NV - 1] = L[NV - 1] - fs * rE;
+    double a2 = 0.0, wc = 0.0, fc = p.f;
+    if (p.use_cmax) {
+      a2 = p.gamma * P / rho;
+      wc = 1.0 + (a2 * a2) * p.inv_cmax4;
+      fc = 1.0 - 1.0 / sqrt(wc);
+    }
+    const double w = mu[0] * r0 + rv * mv + mu[NV - 1] * rE;
+    const double ds = -fc * w, dw = -fc * s, dfc = -s * w;
+    double dv2 = 0.0, drho = 0.0, dP = 0.0, dH = 0.0;
+    if (pform) {
+      nu[0] += ds * p.gm1 * 0.5 * v2;
+      for (int e = 0; e < ND; ++e) {
+        nu[1 + e] -= ds * p.gm1 * v[e];
+        dv[e] -= ds * p.gm1 * dU[1 + e];
+      }
+      nu[NV - 1] += ds * p.gm1;
+      dv2 += ds * p.gm1 * 0.5 * dU[0];
+    } else {
+      nu[0] += ds;
+    }
+    for (int e = 0; e < ND; ++e) dv[e] += dw * rv * mu[1 + e];
+    if (var == RSST_PVS || var == RSST_PMS) {
+      double dia2 = dw * mu[0] + (var == RSST_PVS ? dw * mv : 0.0);
+      const double drE = dw * mu[NV - 1];
+      dH = drE * ia2 / rho;
+      dia2 += drE * H / rho;
+      drho -= drE * rE / rho;
+      drho += dia2 / (p.gamma * P);
+      dP -= dia2 * ia2 / P;
+    } else if (var == RSST_DVS || var == RSST_DMS) {
+      dH = dw * mu[NV - 1] / rho;
+      drho -= dw * mu[NV - 1] * rE / rho;
+    }
+    dP += dH * (p.inv_gm1 + 1.0);
+    const double dkin = sgn * dH;
+    if (p.use_cmax) {
+      const double da2 = dfc * p.inv_cmax4 * a2 / (wc * sqrt(wc));
+      dP += da2 * p.gamma / rho;
+      drho -= da2 * a2 / rho;
+    } else {
+      dfc_total = dfc;
+    }
+    drho += dkin * 0.5 * v2;
+    dv2 += dkin * 0.5 * rho;
+    dq[NV - 1] += dP * p.gm1;
+    drho -= dP * p.gm1 * 0.5 * v2;
+    dv2 -= dP * p.gm1 * 0.5 * rho;
+    for (int e = 0; e < ND; ++e) {
+      dv[e] += 2.0 * v[e] * dv2;
+      dq[1 + e] += dv[e] / rho;
+      drho -= dv[e] * v[e] / rho;
+    }
+    dq[0] += drho;
   }
   if (p.has_grav) {
-    T mg = q[0] * 0.0;
     for (int e = 0; e < ND; ++e) {
-      L[1 + e] = L[1 + e] + rho * p.grav[e];
-      mg = mg + q[1 + e] * p.grav[e];
+      dq[0] += mu[1 + e] * p.grav[e];
+      dq[1 + e] += mu[NV - 1] * p.grav[e];
     }
-    L[NV - 1] = L[NV - 1] + mg;
   }
+  return dfc_total;
 }
 
 struct AdjArgs {
@@ -226,43 +364,22 @@ __global__ void __launch_bounds__(128) adj_cell_kernel(AdjArgs a) {
         int cf[3] = {c[0], c[1], c[2]};
         cf[d] += side;  // face cf[d] - 1/2
         double s[4][NV], F[NV];
-        if (d == 0) { load_stencil<NV, 0>(a, cf, s); face_T<double, NV, 0>(s[0], s[1], s[2], s[3], p, p.inv_xi, F); }
-        if (d == 1) { if constexpr (ND >= 2) { load_stencil<NV, 1>(a, cf, s); face_T<double, NV, 1>(s[0], s[1], s[2], s[3], p, p.inv_xi, F); } }
-        if (d == 2) { if constexpr (ND >= 3) { load_stencil<NV, 2>(a, cf, s); face_T<double, NV, 2>(s[0], s[1], s[2], s[3], p, p.inv_xi, F); } }
+        if (d == 0) { load_stencil<NV, 0>(a, cf, s); face_flux<NV, 0>(s, p, F); }
+        if (d == 1) { if constexpr (ND >= 2) { load_stencil<NV, 1>(a, cf, s); face_flux<NV, 1>(s, p, F); } }
+        if (d == 2) { if constexpr (ND >= 3) { load_stencil<NV, 2>(a, cf, s); face_flux<NV, 2>(s, p, F); } }
         const double sg = side == 0 ? 1.0 : -1.0;
         for (int v = 0; v < NV; ++v) dU[v] += sg * F[v] * p.inv_dx[d];
       }
     }
-    // nu = mu^T dL/d(dU), pointwise mu^T dL/dq, xi partial
-    Dual qd[NV], dd[NV], L[NV];
-    const Dual f0 = mk(p.f);
-    for (int j = 0; j < NV; ++j) {
-      for (int v = 0; v < NV; ++v) {
-        qd[v] = mk(q[v]);
-        dd[v] = mk(dU[v], v == j ? 1.0 : 0.0);
-      }
-      rhs_T<Dual, NV>(qd, dd, f0, p, L);
-      double acc = 0.0;
-      for (int v = 0; v < NV; ++v) acc += mu[v] * L[v].d;
-      a.nu[j * g.fstride + o] = acc;
-    }
-    for (int j = 0; j < NV; ++j) {
-      for (int v = 0; v < NV; ++v) {
-        qd[v] = mk(q[v], v == j ? 1.0 : 0.0);
-        dd[v] = mk(dU[v]);
-      }
-      rhs_T<Dual, NV>(qd, dd, f0, p, L);
-      double acc = 0.0;
-      for (int v = 0; v < NV; ++v) acc += mu[v] * L[v].d;
-      a.lam[j * g.fstride + o] = acc;
-    }
+    // nu = mu^T dL/d(dU), pointwise mu^T dL/dq, xi partial (f = 1 - 1/xi^2)
+    double nu[NV], dq[NV];
+    const double df = rhs_vjp<NV>(q, dU, mu, p, nu, dq);
     for (int v = 0; v < NV; ++v) {
-      qd[v] = mk(q[v]);
-      dd[v] = mk(dU[v]);
+      a.nu[v * g.fstride + o] = nu[v];
+      a.lam[v * g.fstride + o] = dq[v];
     }
     const double xi = p.xi;
-    rhs_T<Dual, NV>(qd, dd, mk(p.f, 2.0 / (xi * xi * xi)), p, L);  // f = 1 - 1/xi^2
-    for (int v = 0; v < NV; ++v) dxi += mu[v] * L[v].d;
+    dxi = df * 2.0 / (xi * xi * xi);
   }
   block_sum_to(dxi, a.part + blockIdx.x, sh);
 }
@@ -296,24 +413,13 @@ __global__ void __launch_bounds__(128) adj_face_kernel(AdjArgs a, int part_off) 
         phi[v] = (nr - nl) * p.inv_dx[D];
       }
     }
-    double* G = a.faceG + (a.face_off[D] + id) * (4 * NV);
-    Dual sd[4][NV], F[NV];
-    const Dual ix = mk(p.inv_xi);
-    for (int k = 0; k < 4; ++k) {
-      for (int j = 0; j < NV; ++j) {
-        for (int kk = 0; kk < 4; ++kk)
-          for (int v = 0; v < NV; ++v) sd[kk][v] = mk(s[kk][v], (kk == k && v == j) ? 1.0 : 0.0);
-        face_T<Dual, NV, D>(sd[0], sd[1], sd[2], sd[3], p, ix, F);
-        double acc = 0.0;
-        for (int v = 0; v < NV; ++v) acc += phi[v] * F[v].d;
-        G[k * NV + j] = acc;
-      }
-    }
-    for (int kk = 0; kk < 4; ++kk)
-      for (int v = 0; v < NV; ++v) sd[kk][v] = mk(s[kk][v]);
+    double G[4][NV];
+    const double dinv_xi = face_vjp<NV, D>(s, phi, p, G);
+    double* dst = a.faceG + (a.face_off[D] + id) * (4 * NV);
+    for (int k = 0; k < 4; ++k)
+      for (int v = 0; v < NV; ++v) dst[k * NV + v] = G[k][v];
     const double xi = p.xi;
-    face_T<Dual, NV, D>(sd[0], sd[1], sd[2], sd[3], p, mk(p.inv_xi, -1.0 / (xi * xi)), F);
-    for (int v = 0; v < NV; ++v) dxi += phi[v] * F[v].d;
+    dxi = -dinv_xi / (xi * xi);  // 1/xi -> xi
   }
   block_sum_to(dxi, a.part + part_off + blockIdx.x, sh);
 }
