@@ -234,6 +234,35 @@ def run_modes(dev, peaks, sm_mhz):
                                               "dtype": "f32x2 double-float (48-bit significand), parity 1e-10 vs f64"})
     out["fp32_pert_polytrope_3d"] = _mode_line(w, "fp32_pert", _time_single(w, "fp32_pert", 20, 3, dev, False), 20,
                                                peaks, {"bound": "hbm (instruction-issue limited)"})
+    # 1D N=256 sound wave, 2000 steps: launch-bound; CUDA-graph blocks vs plain launches
+    w = inputs.sound_wave_1d(256, xi=10.0, variant="pvs")
+    for k, name in ((16, "fp64_sound1d_256_graph"), (0, "fp64_sound1d_256_plain")):
+        stream = torch.cuda.current_stream(dev)
+        s = rsst.Solver(w, "fp64", stream=stream)
+        s.set_graph_steps(k)
+        s.set_state(torch.from_numpy(w["U"]).to(dev))
+        s.step(64)
+        s.sync()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s.step(2000)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        s.sync()
+        s.close()
+        t = e0.elapsed_time(e1) / 1e3
+        out[name] = {"value": 256 * 2 * 2000 / t, "unit": UNIT, "steps_per_s": 2000 / t, "steps": 2000,
+                     "graph_steps": k, "bound": "launch latency"}
+    # 2D 4096^2 shear layer: the HBM-regime point of the 2D configuration
+    w = inputs.shear_layer_2d(4096, 4096, xi=30.0, variant="pvs")
+    out["fp64_shear_4096"] = _mode_line(w, "fp64", _time_single(w, "fp64", 3, 2, dev, False), 3, peaks,
+                                        {"bound": "alu (float64)"})
+    out["fp32_pert_shear_4096"] = _mode_line(w, "fp32_pert", _time_single(w, "fp32_pert", 10, 3, dev, False), 10,
+                                             peaks, {"bound": "hbm (instruction-issue limited)"})
+    out["fp64_df_shear_4096"] = _mode_line(w, "fp64", _time_single(w, "fp64_df", 5, 2, dev, False), 5, peaks,
+                                           {"bound": "alu (float32 pipe, double-float arithmetic)",
+                                            "dtype": "f32x2 double-float (48-bit significand), parity 1e-10 vs f64"})
+    del w
     # adjoint: 2D 256^2 stratified box, 400 steps, checkpoint every 20
     w = inputs.polytrope_2d(256, 256, xi=20.0, contrast=20.0, amp=1e-3)
     s = rsst.Solver(w, "fp64", stream=torch.cuda.current_stream(dev))

@@ -122,8 +122,17 @@ int rsst_get_state(rsst_handle* h, double* U, int on_host);
  * each step takes dt = cfl / max_cells sum_d c_tot/dx_d from the state at
  * its start, entirely on the device.  Each step is two fused stage kernels
  * (reconstruction, LLF flux, divergence, RSST correction, force, RK update,
- * ghost cells; the second also reduces the CFL maximum).  Asynchronous. */
+ * ghost cells; the second also reduces the CFL maximum).  Whole blocks of
+ * rsst_set_graph_steps() steps replay a captured CUDA graph; the results
+ * are the same as with plain launches.  Asynchronous. */
 int rsst_step(rsst_handle* h, double dt, int nsteps);
+
+/* Steps per replayed CUDA graph in rsst_step (default 16; 0 = plain
+ * launches only).  k must be even and >= 0, else RSST_EINVAL.  A graph is
+ * captured per CFL-slot parity on first use and again when a fixed dt
+ * changes.  This is a launch-overhead control for small grids: the paper
+ * has no counterpart. */
+int rsst_set_graph_steps(rsst_handle* h, int32_t k);
 
 /* The step the next adaptive rsst_step will take (cfl / CFL maximum of the
  * current state).  Synchronous. */

@@ -166,9 +166,18 @@ static void make_phys(const rsst_config* c, Phys* p) {
   }
 }
 
+static void drop_graphs(rsst_handle* h) {
+  for (int p = 0; p < 2; ++p) {
+    if (h->gvalid[p]) cudaGraphExecDestroy(h->gexec[p]);
+    h->gvalid[p] = 0;
+  }
+}
+
 extern "C" void rsst_destroy(rsst_handle* h) {
   if (!h) return;
   rsst_adjoint_free(h);
+  drop_graphs(h);
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   cudaFree(h->buf[0]);
   cudaFree(h->buf[1]);
   cudaFree(h->d_bg);
@@ -191,6 +200,7 @@ extern "C" int rsst_init(rsst_handle** out, const rsst_config* cfg, void* stream
   h->cfg.bg_rho = nullptr;
   h->cfg.bg_p = nullptr;
   h->stream = (cudaStream_t)stream;
+  h->graph_steps = RSST_DEFAULT_GRAPH_STEPS;
   h->elem = cfg->precision == RSST_FP32_PERT ? sizeof(float) : sizeof(double);  // a double-float is 8 bytes
   make_geom(cfg, h->elem, &h->g);
   make_phys(cfg, &h->p);
@@ -326,7 +336,7 @@ extern "C" int rsst_get_state(rsst_handle* h, double* U, int on_host) {
 }
 
 template <typename T>
-static int run_steps(rsst_handle* h, double dt, int nsteps) {
+static int plain_steps(rsst_handle* h, double dt, int nsteps, cudaStream_t st) {
   StageArgs<T> a;
   memset(&a, 0, sizeof a);
   a.g = h->g;
@@ -347,30 +357,103 @@ static int run_steps(rsst_handle* h, double dt, int nsteps) {
     a.in = U;
     a.base = nullptr;
     a.out = Us;
-    if constexpr (std::is_same<T, double>::value) RC_TRY(rsst_launch_stage_fp64(a, h->stream));
-    else if constexpr (std::is_same<T, float2>::value) RC_TRY(rsst_launch_stage_df(a, h->stream));
-    else if (h->use_tma2d) RC_TRY(rsst_launch_stage2d_tma(&h->tmap[0], a, h->stream));
-    else if (h->use_tma3d) RC_TRY(rsst_launch_stage3d_tma(&h->tmap[0], a, h->stream));
-    else RC_TRY(rsst_launch_stage_fp32(a, h->stream));
+    if constexpr (std::is_same<T, double>::value) RC_TRY(rsst_launch_stage_fp64(a, st));
+    else if constexpr (std::is_same<T, float2>::value) RC_TRY(rsst_launch_stage_df(a, st));
+    else if (h->use_tma2d) RC_TRY(rsst_launch_stage2d_tma(&h->tmap[0], a, st));
+    else if (h->use_tma3d) RC_TRY(rsst_launch_stage3d_tma(&h->tmap[0], a, st));
+    else RC_TRY(rsst_launch_stage_fp32(a, st));
     a.stage = 2;
     a.in = Us;
     a.base = U;
     a.out = U;
-    if constexpr (std::is_same<T, double>::value) RC_TRY(rsst_launch_stage_fp64(a, h->stream));
-    else if constexpr (std::is_same<T, float2>::value) RC_TRY(rsst_launch_stage_df(a, h->stream));
-    else if (h->use_tma2d) RC_TRY(rsst_launch_stage2d_tma(&h->tmap[1], a, h->stream));
-    else if (h->use_tma3d) RC_TRY(rsst_launch_stage3d_tma(&h->tmap[1], a, h->stream));
-    else RC_TRY(rsst_launch_stage_fp32(a, h->stream));
+    if constexpr (std::is_same<T, double>::value) RC_TRY(rsst_launch_stage_fp64(a, st));
+    else if constexpr (std::is_same<T, float2>::value) RC_TRY(rsst_launch_stage_df(a, st));
+    else if (h->use_tma2d) RC_TRY(rsst_launch_stage2d_tma(&h->tmap[1], a, st));
+    else if (h->use_tma3d) RC_TRY(rsst_launch_stage3d_tma(&h->tmap[1], a, st));
+    else RC_TRY(rsst_launch_stage_fp32(a, st));
     h->launches += 2;
     h->slot ^= 1;
   }
   return RSST_OK;
 }
 
+// Capture graph_steps steps starting at the current slot parity on the
+// private capture stream (nothing runs during capture) and instantiate them.
+template <typename T>
+static int build_graph(rsst_handle* h, double dt) {
+  const int p = h->slot;
+  if (h->gvalid[p]) {
+    cudaGraphExecDestroy(h->gexec[p]);
+    h->gvalid[p] = 0;
+  }
+  if (!h->cap_stream && cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    h->cap_stream = nullptr;
+    rsst_set_error("could not create the graph capture stream");
+    return RSST_ECUDA;
+  }
+  if (cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGetLastError();
+    rsst_set_error("cudaStreamBeginCapture failed");
+    return RSST_ECUDA;
+  }
+  const int64_t launches = h->launches;
+  const int rc = plain_steps<T>(h, dt, h->graph_steps, h->cap_stream);
+  h->launches = launches;
+  h->slot = p;  // an even number of steps: the parity is unchanged
+  cudaGraph_t g = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(h->cap_stream, &g);
+  if (rc != RSST_OK || e != cudaSuccess || cudaGraphInstantiate(&h->gexec[p], g, 0) != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    if (rc == RSST_OK) rsst_set_error("graph capture of the step failed");
+    return rc != RSST_OK ? rc : RSST_ECUDA;
+  }
+  cudaGraphDestroy(g);
+  h->gvalid[p] = 1;
+  h->gdt[p] = dt;
+  return RSST_OK;
+}
+
+// nsteps SSP-RK2 steps: whole blocks of graph_steps steps replay a captured
+// graph on the caller's stream, the rest are plain launches.
+template <typename T>
+static int run_steps(rsst_handle* h, double dt, int nsteps) {
+  const int K = h->graph_steps;
+  if (K > 0 && nsteps >= K) {
+    if (!h->graph_warm) {  // first launch sets the kernels' attributes outside any capture
+      RC_TRY(plain_steps<T>(h, dt, 1, h->stream));
+      h->graph_warm = 1;
+      --nsteps;
+    }
+    while (nsteps >= K) {
+      const int p = h->slot;
+      if (!h->gvalid[p] || h->gdt[p] != dt) RC_TRY(build_graph<T>(h, dt));
+      if (cudaGraphLaunch(h->gexec[p], h->stream) != cudaSuccess) {
+        rsst_set_error("graph launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+        return RSST_ECUDA;
+      }
+      h->launches += 2 * (int64_t)K;
+      nsteps -= K;
+    }
+  }
+  return plain_steps<T>(h, dt, nsteps, h->stream);
+}
+
 int rsst_handle_steps(rsst_handle* h, double dt, int nsteps) {
   if (h->cfg.precision == RSST_FP32_PERT) return run_steps<float>(h, dt, nsteps);
   if (h->cfg.precision == RSST_FP64_DF) return run_steps<float2>(h, dt, nsteps);
   return run_steps<double>(h, dt, nsteps);
+}
+
+extern "C" int rsst_set_graph_steps(rsst_handle* h, int32_t k) {
+  if (!h || k < 0 || (k & 1)) {
+    rsst_set_error("rsst_set_graph_steps: need a handle and an even k >= 0");
+    return RSST_EINVAL;
+  }
+  if (k != h->graph_steps) drop_graphs(h);
+  h->graph_steps = k;
+  return RSST_OK;
 }
 
 extern "C" int rsst_step(rsst_handle* h, double dt, int nsteps) {

@@ -590,7 +590,10 @@ static int launch_stage32(const StageArgs<float>& a, cudaStream_t s) {
 
 template <int NDIM, int VERT>
 static int launch_stage32_dim(const StageArgs<float>& a, cudaStream_t s) {
-  if constexpr (NDIM == 1) return launch_stage32<1, VERT, 256, 1, 1, 256>(a, s);
+  if constexpr (NDIM == 1) {
+    if (a.g.n[0] <= RSST_SMALL_1D) return launch_stage32<1, VERT, 16, 1, 1, 32>(a, s);
+    return launch_stage32<1, VERT, 256, 1, 1, 256>(a, s);
+  }
   if constexpr (NDIM == 2) return launch_stage32<2, VERT, 64, 16, 1, 256>(a, s);
   if constexpr (NDIM == 3) return launch_stage32<3, VERT, 32, 8, 4, 256>(a, s);
   return RSST_EINVAL;

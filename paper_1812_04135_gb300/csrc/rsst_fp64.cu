@@ -384,7 +384,9 @@ using namespace rsst;
 
 int rsst_launch_stage_fp64(const StageArgs<double>& a, cudaStream_t s) {
   switch (a.g.ndim) {
-    case 1: return launch_stage<1, 256, 1, 1, 256>(a, s);
+    case 1:  // short lines: 16-cell tiles (17 faces, one per thread of a warp) spread the float64 work over SMs
+      if (a.g.n[0] <= RSST_SMALL_1D) return launch_stage<1, 16, 1, 1, 32>(a, s);
+      return launch_stage<1, 256, 1, 1, 256>(a, s);
     case 2: return launch_stage<2, 32, 16, 1, 256>(a, s);
     case 3: return launch_stage<3, 16, 8, 4, 256>(a, s);
   }

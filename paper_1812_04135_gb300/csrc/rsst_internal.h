@@ -8,6 +8,10 @@
 #include "rsst.h"
 
 #define RSST_G 2  // ghost layers per end of an active axis (MUSCL needs i-2..i+2)
+#define RSST_DEFAULT_GRAPH_STEPS 16  // steps per replayed CUDA graph (even)
+// 1D lines up to this length use 16-cell tiles (one warp each, one face per
+// thread), so that a short line runs on many SMs instead of one CTA on one SM
+#define RSST_SMALL_1D (32 * 152 * 4)
 
 // Padded device layout of one run's state, per field:
 //   interior cell (i, j, k) lives at  (k + gz) * plane + (j + gy) * pitch + (i + xoff)
@@ -146,6 +150,15 @@ struct rsst_handle {
   void* adj;            // adjoint checkpoints and work arrays, or null
   int slot;
   int64_t launches;
+  // CUDA-graph replay of blocks of graph_steps steps (0: plain launches).
+  // One executable graph per CFL-slot parity; graph_steps is even, so a
+  // block leaves the parity unchanged.  Captured on cap_stream.
+  int graph_steps;
+  int graph_warm;           // a plain step ran (one-time kernel attributes set)
+  cudaStream_t cap_stream;
+  cudaGraphExec_t gexec[2];
+  int gvalid[2];
+  double gdt[2];            // the dt each graph was captured with
 };
 
 void rsst_adjoint_free(rsst_handle* h);

@@ -56,6 +56,7 @@ def lib():
             "rsst_set_state": (i32, [vp, vp, i32]),
             "rsst_get_state": (i32, [vp, vp, i32]),
             "rsst_step": (i32, [vp, dbl, i32]),
+            "rsst_set_graph_steps": (i32, [vp, i32]),
             "rsst_dt": (i32, [vp, pd]),
             "rsst_sync": (i32, [vp]),
             "rsst_time": (i32, [vp, pd]),
@@ -227,6 +228,10 @@ def rsst_math_selftest(n: int = 1 << 20):
     return ulp.value, bad.value
 
 
+def rsst_set_graph_steps(h: int, k: int) -> None:
+    _check(lib().rsst_set_graph_steps(h, int(k)), "rsst_set_graph_steps")
+
+
 def rsst_kernel_launches(h: int) -> int:
     return int(lib().rsst_kernel_launches(h))
 
@@ -261,6 +266,9 @@ class Solver:
 
     def step(self, nsteps: int = 1, dt: float = 0.0) -> None:
         rsst_step(self.h, dt, nsteps)
+
+    def set_graph_steps(self, k: int) -> None:
+        rsst_set_graph_steps(self.h, k)
 
     def dt(self) -> float:
         return rsst_dt(self.h)

@@ -58,3 +58,8 @@ def test_invalid_config_rejected_without_gpu(L, bad):
     with pytest.raises(rsst.RsstError) as e:
         rsst.rsst_init(cfg, stream=0)
     assert e.value.code == rsst.RSST_EINVAL
+
+
+def test_graph_steps_rejects_null_handle_and_odd_k(L):
+    assert L.rsst_set_graph_steps(None, 16) == rsst.RSST_EINVAL
+    assert L.rsst_set_graph_steps(None, 3) == rsst.RSST_EINVAL

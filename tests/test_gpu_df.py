@@ -90,3 +90,8 @@ def test_momentum_conserved_and_flag():
         s.sync()
     assert e.value.code == rsst.RSST_ENONPHYSICAL
     s.close()
+
+
+@pytest.mark.parametrize("n", [19456, 20011])
+def test_long_1d_lines_use_wide_tiles(n):
+    check(inputs.random_smooth_state(1, (n,), xi=6.0, variant="dms"), 3, what=n)

@@ -122,3 +122,8 @@ def test_cmax_law_float32():
               inputs.polytrope_3d(20, 12, 40, xi=1.0, amp=1e-3, contrast=20.0)):
         w["cmax"] = 0.05
         check(w, 5, what=w["name"])
+
+
+@pytest.mark.parametrize("n", [19456, 20011])
+def test_long_1d_lines_use_wide_tiles(n):
+    check(inputs.random_smooth_state(1, (n,), xi=6.0, variant="pvs"), 3, tol=TOL, what=n)

@@ -208,3 +208,11 @@ def test_cmax_stratified_background():
     w = inputs.polytrope_2d(40, 70, xi=1.0, contrast=20.0, amp=1e-2)
     w["cmax"] = 0.05
     _assert_close(gpu_run(w, 6), oracle_run(w, 6), w["gamma"])
+
+
+@pytest.mark.parametrize("n", [19456, 19457, 20011])
+def test_long_1d_lines_use_wide_tiles(n):
+    """Lines up to 32*152*4 cells run in 32-cell tiles, longer ones in
+    256-cell tiles: both shapes, and the boundary between them, match."""
+    w = inputs.random_smooth_state(1, (n,), xi=6.0, variant="pvs", bc=("reflect",), grav=(0.5, 0.0, 0.0))
+    _assert_close(gpu_run(w, 3), oracle_run(w, 3), w["gamma"], what=n)
