@@ -247,13 +247,17 @@ int rsst_conserved_sums_noalloc(const double* U, int32_t ndim, const int32_t* n,
 /* Number of kernels the library launched through this handle so far. */
 int64_t rsst_kernel_launches(const rsst_handle* h);
 
-/* Self-test of two float64 helpers the kernels use in place of compiler
+/* Self-test of the float64 helpers the kernels use in place of compiler
  * sequences (no counterpart in the paper): over n seeded inputs, the largest
  * difference in ulps between the Newton-Raphson reciprocal and CUDA's
- * correctly rounded 1.0/x (x in [2^-20, 2^20]), and the number of inputs on
- * which the integer-pipe MC limiter differs from the direct float64 form.
- * Synchronous, current device. */
-int rsst_math_selftest(int32_t n, double* rcp_max_ulp, int32_t* mc_mismatches);
+ * correctly rounded 1.0/x (x in [2^-20, 2^20]); the number of inputs on
+ * which the integer-pipe MC limiter differs from the direct float64 form
+ * (plus 2^20 if the c_tot square root misses one of its special cases: 0
+ * and subnormal -> 0, negative -> NaN); and the largest relative
+ * difference between the c_tot square root and CUDA's sqrt (x in
+ * [2^-200, 2^200]).  All outputs are host pointers.  Synchronous, current
+ * device. */
+int rsst_math_selftest(int32_t n, double* rcp_max_ulp, int32_t* mc_mismatches, double* sqrt_max_rel);
 
 /* sizeof(rsst_config) as compiled into the library (binding check). */
 size_t rsst_config_size(void);

@@ -45,12 +45,39 @@ __device__ __forceinline__ double rcp_nr(double x) {
   return fma(y, e, y);
 }
 
+// sqrt(x) for the wave-speed estimate c_tot with three float64-pipe
+// operations.  Seed: the float32 hardware reciprocal square root of
+// m 2^odd, where x = m 2^e (m in [1, 2) holding x's leading 23 mantissa
+// bits) and odd = e mod 2, so the argument lies in [1, 4); the result is
+// rescaled by 2^(-(e - odd)/2) in the exponent field, all on the integer
+// pipe.  One Newton step in Markstein's form, s = s0 + (y0/2)(x - s0^2) with
+// s0 = x y0 and the residual x - s0^2 formed exactly by an FMA, squares the
+// seed's relative error (about 2^-21) to below 2^-40.  Zero and subnormal x
+// give 0, negative x NaN.  c_tot only sets the LLF dissipation speed and the
+// CFL step, where this error is far below the 1e-10 the float64 path is
+// held to; every other square root is the compiler's.
+__device__ __forceinline__ double sqrt_ctot(double x) {
+  const long long ix = __double_as_longlong(x);
+  const int be = (int)(ix >> 52);  // biased exponent for x >= 0
+  const int e = be - 1023;
+  const int odd = e & 1;
+  const float f = __int_as_float(((127 + odd) << 23) | (int)((ix >> 29) & 0x7fffff));
+  const int ir = __float_as_int(rsqrtf(f));  // in (1/2, 1]
+  const int k = (e - odd) >> 1;              // 1/sqrt(x) = rsqrt(f) 2^(-k)
+  const long long yb = ((long long)(((ir >> 23) & 0xff) - 127 + 1023 - k) << 52) | ((long long)(ir & 0x7fffff) << 29);
+  const double y0 = __longlong_as_double(yb);
+  const double h0 = __longlong_as_double(yb - (1ll << 52));  // y0 / 2
+  const double s0 = x * y0;
+  const double s = fma(h0, fma(-s0, s0, x), s0);
+  return be > 0 ? s : (ix >= 0 ? 0.0 : __longlong_as_double(0x7ff8000000000000ll));
+}
+
 // Effective sound speed a/xi from a^2 and the factor f = 1 - 1/xi^2: constant
 // xi, or the C_max law xi = [1 + (a/C_max)^4]^(1/4) (Eq. cx, Sec. 4.3), for
 // which a/xi = sqrt(a^2 / sqrt(w)) and f = 1 - 1/sqrt(w), w = 1 + a^4/C_max^4.
 __device__ __forceinline__ double sound_over_xi(double a2, const Phys& p) {
   if (p.use_cmax) return sqrt(a2 / sqrt(fma(a2 * a2, p.inv_cmax4, 1.0)));
-  return sqrt(a2) * p.inv_xi;
+  return sqrt_ctot(a2) * p.inv_xi;
 }
 __device__ __forceinline__ double f_of(double a2, const Phys& p) {
   if (p.use_cmax) return 1.0 - 1.0 / sqrt(fma(a2 * a2, p.inv_cmax4, 1.0));
@@ -73,7 +100,7 @@ __device__ __forceinline__ void euler_flux(const double (&q)[NV], const Phys& p,
     v2 += v[e] * v[e];
   }
   const double P = Eos::pressure(p, rho, q[NV - 1], rho * v2);
-  c = sqrt(v2) + sound_over_xi(Eos::sound2(p, rho, P, ir), p);
+  c = sqrt_ctot(v2) + sound_over_xi(Eos::sound2(p, rho, P, ir), p);
   // half fluxes: the LLF average of the two sides needs F/2
   const double hv = 0.5 * v[D];
   F[0] = 0.5 * q[1 + D];
@@ -192,7 +219,7 @@ __device__ __forceinline__ double cfl_rate(const double (&q)[NV], const Phys& p,
   }
   const double P = Eos::pressure(p, rho, q[NV - 1], rho * v2);
   ok = fin && rho > 0.0 && P > 0.0;
-  const double c = sqrt(v2) + sound_over_xi(Eos::sound2(p, rho, P, ir), p);
+  const double c = sqrt_ctot(v2) + sound_over_xi(Eos::sound2(p, rho, P, ir), p);
   return c * p.sum_inv_dx;
 }
 

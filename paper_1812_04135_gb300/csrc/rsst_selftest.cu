@@ -1,7 +1,9 @@
 // Device self-test of the float64 helpers the kernels use instead of the
 // compiler's sequences: the Newton-Raphson reciprocal against CUDA's
-// correctly rounded division (largest error in ulps), and the integer-pipe
-// MC limiter against the direct float64 form of the same definition.
+// correctly rounded division (largest error in ulps), the integer-pipe MC
+// limiter against the direct float64 form of the same definition, and the
+// c_tot square root against CUDA's sqrt (largest relative error, plus its
+// zero, subnormal and negative cases).
 #include <cmath>
 #include <cstring>
 
@@ -24,7 +26,8 @@ __device__ __forceinline__ unsigned long long smix(unsigned long long z) {
   return z ^ (z >> 31);
 }
 
-__global__ void selftest_kernel(int n, unsigned long long* max_ulp, unsigned int* mc_bad) {
+__global__ void selftest_kernel(int n, unsigned long long* max_ulp, unsigned int* mc_bad,
+                                unsigned long long* sqrt_rel_bits) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const unsigned long long r1 = smix(2 * (unsigned long long)i), r2 = smix(2 * (unsigned long long)i + 1);
@@ -46,29 +49,39 @@ __global__ void selftest_kernel(int n, unsigned long long* max_ulp, unsigned int
   if (__double_as_longlong(mc_slope(a, b)) != __double_as_longlong(mc_direct(a, b)) &&
       !(mc_slope(a, b) == 0.0 && mc_direct(a, b) == 0.0))
     atomicAdd(mc_bad, 1u);
+  // c_tot square root over 1e-60 .. 1e60, exact squares and powers of two
+  double xs = exp2(-200.0 + 400.0 * u2);
+  if (mode == 6) xs = exp2((double)((int)(u1 * 400.0) - 200));
+  if (mode == 7) xs = (1.0 + u1) * (1.0 + u1);
+  const double rel = fabs(sqrt_ctot(xs) - sqrt(xs)) / sqrt(xs);
+  atomicMax(sqrt_rel_bits, (unsigned long long)__double_as_longlong(rel));  // non-negative: bits order as values
+  if (i == 0) {
+    const bool specials = sqrt_ctot(0.0) == 0.0 && sqrt_ctot(4.9e-324) == 0.0 && isnan(sqrt_ctot(-1.0));
+    if (!specials) atomicAdd(mc_bad, 1u << 20);
+  }
 }
 
 }  // namespace rsst
 
-extern "C" int rsst_math_selftest(int32_t n, double* rcp_max_ulp, int32_t* mc_mismatches) {
-  if (n < 1 || !rcp_max_ulp || !mc_mismatches) {
+extern "C" int rsst_math_selftest(int32_t n, double* rcp_max_ulp, int32_t* mc_mismatches, double* sqrt_max_rel) {
+  if (n < 1 || !rcp_max_ulp || !mc_mismatches || !sqrt_max_rel) {
     rsst_set_error("rsst_math_selftest: bad arguments");
     return RSST_EINVAL;
   }
-  unsigned long long* d_ulp = nullptr;
+  unsigned long long* d_ulp = nullptr;  // [0] rcp ulps, [1] sqrt relative error bits
   unsigned int* d_bad = nullptr;
-  if (cudaMalloc((void**)&d_ulp, sizeof(*d_ulp)) != cudaSuccess || cudaMalloc((void**)&d_bad, sizeof(*d_bad)) != cudaSuccess) {
+  if (cudaMalloc((void**)&d_ulp, 2 * sizeof(*d_ulp)) != cudaSuccess || cudaMalloc((void**)&d_bad, sizeof(*d_bad)) != cudaSuccess) {
     cudaGetLastError();
     cudaFree(d_ulp);
     rsst_set_error("rsst_math_selftest: allocation failed");
     return RSST_ENOMEM;
   }
-  cudaMemset(d_ulp, 0, sizeof(*d_ulp));
+  cudaMemset(d_ulp, 0, 2 * sizeof(*d_ulp));
   cudaMemset(d_bad, 0, sizeof(*d_bad));
-  rsst::selftest_kernel<<<(n + 255) / 256, 256>>>(n, d_ulp, d_bad);
-  unsigned long long ulp = 0;
+  rsst::selftest_kernel<<<(n + 255) / 256, 256>>>(n, d_ulp, d_bad, d_ulp + 1);
+  unsigned long long ulp[2] = {0, 0};
   unsigned int bad = 0;
-  const cudaError_t e1 = cudaMemcpy(&ulp, d_ulp, sizeof ulp, cudaMemcpyDeviceToHost);
+  const cudaError_t e1 = cudaMemcpy(ulp, d_ulp, sizeof ulp, cudaMemcpyDeviceToHost);
   const cudaError_t e2 = cudaMemcpy(&bad, d_bad, sizeof bad, cudaMemcpyDeviceToHost);
   cudaFree(d_ulp);
   cudaFree(d_bad);
@@ -76,7 +89,10 @@ extern "C" int rsst_math_selftest(int32_t n, double* rcp_max_ulp, int32_t* mc_mi
     rsst_set_error("rsst_math_selftest: %s", cudaGetErrorString(e1 != cudaSuccess ? e1 : e2));
     return RSST_ECUDA;
   }
-  *rcp_max_ulp = (double)ulp;
+  *rcp_max_ulp = (double)ulp[0];
   *mc_mismatches = (int32_t)bad;
+  double rel;
+  memcpy(&rel, &ulp[1], sizeof rel);
+  *sqrt_max_rel = rel;
   return RSST_OK;
 }

@@ -64,7 +64,7 @@ def lib():
             "rsst_kernel_launches": (i64, [vp]),
             "rsst_conserved_sums_noalloc": (i32, [vp, i32, C.POINTER(C.c_int32), pd, vp, vp]),
             "rsst_config_size": (C.c_size_t, []),
-            "rsst_math_selftest": (i32, [i32, pd, C.POINTER(C.c_int32)]),
+            "rsst_math_selftest": (i32, [i32, pd, C.POINTER(C.c_int32), pd]),
             "rsst_adjoint_record": (i32, [vp, dbl, i32, i32]),
             "rsst_adjoint_segments": (i32, [vp, C.POINTER(C.c_int32)]),
             "rsst_adjoint_step": (i32, [vp, i32, vp, pd]),
@@ -224,8 +224,9 @@ def rsst_kinetic_energy(h: int, grad=None) -> float:
 def rsst_math_selftest(n: int = 1 << 20):
     ulp = C.c_double()
     bad = C.c_int32()
-    _check(lib().rsst_math_selftest(int(n), C.byref(ulp), C.byref(bad)), "rsst_math_selftest")
-    return ulp.value, bad.value
+    rel = C.c_double()
+    _check(lib().rsst_math_selftest(int(n), C.byref(ulp), C.byref(bad), C.byref(rel)), "rsst_math_selftest")
+    return ulp.value, bad.value, rel.value
 
 
 def rsst_set_graph_steps(h: int, k: int) -> None:

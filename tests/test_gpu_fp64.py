@@ -190,9 +190,11 @@ def test_host_buffers_roundtrip():
 
 def test_float64_helpers_against_cuda():
     """Newton-Raphson reciprocal within 1 ulp of CUDA's 1.0/x; integer-pipe
-    MC limiter identical to the direct float64 form."""
-    ulp, bad = rsst.rsst_math_selftest(1 << 20)
+    MC limiter identical to the direct float64 form; the c_tot square root
+    within 2^-40 of CUDA's sqrt, with its special cases."""
+    ulp, bad, rel = rsst.rsst_math_selftest(1 << 20)
     assert ulp <= 1.0 and bad == 0, (ulp, bad)
+    assert rel <= 2.0 ** -40, rel
 
 
 @pytest.mark.parametrize("ndim", [1, 2, 3])
