@@ -124,21 +124,23 @@ __device__ __forceinline__ void llf_flux(const double (&qL)[NV], const double (&
 
 // Monotonized-central limited slope (named in Sec. 4.2): 0 if ab <= 0, else
 // the smallest in magnitude of 2a, 2b, (a+b)/2, ties in that order.
-// Only a + b uses the float64 pipe.  Non-negative doubles order like their
-// bit patterns, so the magnitude comparisons run on the integer pipe, and
-// scaling a normal double by 2, 4 or 1/2 is an exact change of its exponent
-// field (2|a| <= |a+b|/2 is |a| * 4 <= |a+b|).  Same decisions and values
-// as the direct form for normal operands; differences of physical states
-// are exactly zero or far above the subnormal range.
+// Only a + b uses the float64 pipe.  A double's bit pattern shifted left by
+// one (sign dropped) orders like its magnitude as an unsigned integer, so the
+// magnitude comparisons run on the integer pipe (the shift, unlike a mask of
+// the sign bit, is not turned back into float64 absolute values by the
+// compiler), and scaling a normal double by 2, 4 or 1/2 is an exact change
+// of its exponent field (2|a| <= |a+b|/2 is |a| * 4 <= |a+b|).  Same
+// decisions and values as the direct form for normal operands; differences
+// of physical states are exactly zero or far above the subnormal range.
 __device__ __forceinline__ double mc_slope(double a, double b) {
-  const long long one = 1ll << 52;  // +1 in the exponent field
-  const long long mask = 0x7fffffffffffffffll;
+  const long long one = 1ll << 52;                // +1 in the exponent field
+  const unsigned long long four = 1ull << 54;     // +2 in the shifted exponent field: x4
   const long long ia = __double_as_longlong(a), ib = __double_as_longlong(b);
-  const long long ma = ia & mask, mb = ib & mask;
-  const bool same = ((ia ^ ib) >= 0) && ma != 0 && mb != 0;
+  const unsigned long long ua = (unsigned long long)ia << 1, ub = (unsigned long long)ib << 1;
+  const bool same = ((ia ^ ib) >= 0) && ua != 0 && ub != 0;
   const long long is = __double_as_longlong(a + b);
-  const long long ms = is & mask;
-  const long long pick = (ma <= mb && ma + 2 * one <= ms) ? ia + one : ((mb + 2 * one <= ms) ? ib + one : is - one);
+  const unsigned long long us = (unsigned long long)is << 1;
+  const long long pick = (ua <= ub && ua + four <= us) ? ia + one : ((ub + four <= us) ? ib + one : is - one);
   return same ? __longlong_as_double(pick) : 0.0;
 }
 
