@@ -150,6 +150,7 @@ static void make_phys(const rsst_config* c, Phys* p) {
   p->xi = c->xi;
   p->inv_xi = 1.0 / c->xi;
   p->f = 1.0 - 1.0 / (c->xi * c->xi);
+  p->gamma_xi2 = c->gamma / (c->xi * c->xi);
   p->use_cmax = c->cmax > 0.0;
   p->inv_cmax4 = p->use_cmax ? 1.0 / (c->cmax * c->cmax * c->cmax * c->cmax) : 0.0;
   p->cfl = c->cfl;

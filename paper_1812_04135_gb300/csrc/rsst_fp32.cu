@@ -78,11 +78,11 @@ __global__ void bgtab_kernel(const double* __restrict__ bg, int L, Phys p, float
   if (k >= 2 && k <= L - 3) {
     double qL[NV], qR[NV], Fm[NV], Fp[NV];
     face(k, qL, qR);
-    llf_flux<NV, V>(qL, qR, p, Fm);
+    llf_flux_x2<NV, V>(qL, qR, p, Fm);
     face(k + 1, qL, qR);
-    llf_flux<NV, V>(qL, qR, p, Fp);
+    llf_flux_x2<NV, V>(qL, qR, p, Fp);
     double D0[NV];
-    for (int v = 0; v < NV; ++v) D0[v] = -(Fp[v] - Fm[v]) * p.inv_dx[V];
+    for (int v = 0; v < NV; ++v) D0[v] = -(Fp[v] - Fm[v]) * (0.5 * p.inv_dx[V]);
     put(TB_D0RHO, D0[0]);
     put(TB_D0MV, D0[1 + V]);
     put(TB_D0E, D0[NV - 1]);

@@ -113,13 +113,13 @@ __device__ __forceinline__ void face_pass(const double* __restrict__ su, double*
       qL[v] = um1 + 0.5 * sl;
       qR[v] = u0 - 0.5 * sr;
     }
-    double F[NV];
-    llf_flux<NV, D>(qL, qR, p, F);
+    double F[NV];  // twice the face flux
+    llf_flux_x2<NV, D>(qL, qR, p, F);
 #pragma unroll
     for (int v = 0; v < NV; ++v) sf[v * C::FMAX + fid] = F[v];
   }
   __syncthreads();
-  const double idx = p.inv_dx[D];
+  const double idx = 0.5 * p.inv_dx[D];  // the faces hold 2 F
 #pragma unroll
   for (int c = 0; c < C::CPT; ++c) {
     const int cell = threadIdx.x + c * NT;

@@ -34,6 +34,7 @@ struct Geom {
 struct Phys {
   double gamma, gm1, inv_gm1, hgm1;  // hgm1 = (gamma - 1)/2
   double xi, inv_xi, f;  // f = 1 - 1/xi^2
+  double gamma_xi2;      // gamma / xi^2: (a/xi)^2 = gamma_xi2 P / rho for the ideal gas
   double inv_cmax4;      // 1/C_max^4 (state-dependent xi, Eq. cx), used if use_cmax
   int use_cmax;
   double cfl;

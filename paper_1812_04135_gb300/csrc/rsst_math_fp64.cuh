@@ -22,6 +22,10 @@ struct IdealGasEos {
   __device__ static __forceinline__ double sound2(const Phys& p, double rho, double P, double inv_rho) {
     return p.gamma * P * inv_rho;
   }
+  // (a/xi)^2 for a constant xi, with gamma/xi^2 folded into one constant
+  __device__ static __forceinline__ double sound2_over_xi2(const Phys& p, double rho, double P, double inv_rho) {
+    return p.gamma_xi2 * (P * inv_rho);
+  }
   __device__ static __forceinline__ double internal_energy(const Phys& p, double rho, double P) {
     return P * p.inv_gm1;
   }
@@ -84,7 +88,13 @@ __device__ __forceinline__ double f_of(double a2, const Phys& p) {
   return p.f;
 }
 
-// Half the Euler flux along dimension D, F/2, and the approximate RSST
+// a/xi of a state for c_tot: constant xi as sqrt((a/xi)^2), or the C_max law.
+__device__ __forceinline__ double ctot_sound(const Phys& p, double rho, double P, double ir) {
+  if (p.use_cmax) return sound_over_xi(Eos::sound2(p, rho, P, ir), p);
+  return sqrt_ctot(Eos::sound2_over_xi2(p, rho, P, ir));
+}
+
+// The Euler flux along dimension D, F, and the approximate RSST
 // characteristic speed c_tot = |V| + a/xi of one state (Eq. pvs_dt0; Sec. 4.2).
 template <int NV, int D>
 __device__ __forceinline__ void euler_flux(const double (&q)[NV], const Phys& p,
@@ -100,26 +110,26 @@ __device__ __forceinline__ void euler_flux(const double (&q)[NV], const Phys& p,
     v2 += v[e] * v[e];
   }
   const double P = Eos::pressure(p, rho, q[NV - 1], rho * v2);
-  c = sqrt_ctot(v2) + sound_over_xi(Eos::sound2(p, rho, P, ir), p);
-  // half fluxes: the LLF average of the two sides needs F/2
-  const double hv = 0.5 * v[D];
-  F[0] = 0.5 * q[1 + D];
+  c = sqrt_ctot(v2) + ctot_sound(p, rho, P, ir);
+  F[0] = q[1 + D];
 #pragma unroll
-  for (int e = 0; e < ND; ++e) F[1 + e] = (e == D) ? fma(q[1 + e], hv, 0.5 * P) : q[1 + e] * hv;
-  F[NV - 1] = (q[NV - 1] + P) * hv;
+  for (int e = 0; e < ND; ++e) F[1 + e] = (e == D) ? fma(q[1 + e], v[D], P) : q[1 + e] * v[D];
+  F[NV - 1] = (q[NV - 1] + P) * v[D];
 }
 
-// Local Lax-Friedrichs flux with alpha = max(c_tot(qL), c_tot(qR)), ties to
-// the left state (Sec. 4.2, step 4).
+// Twice the local Lax-Friedrichs flux, 2 F = F(qL) + F(qR) - alpha (qR - qL)
+// with alpha = max(c_tot(qL), c_tot(qR)), ties to the left state (Sec. 4.2,
+// step 4).  The factor 1/2 is exact and left to the caller (it folds into
+// the divergence's 1/dx), which saves the halvings inside the fluxes.
 template <int NV, int D>
-__device__ __forceinline__ void llf_flux(const double (&qL)[NV], const double (&qR)[NV],
-                                         const Phys& p, double (&F)[NV]) {
-  double FL[NV], FR[NV], cL, cR;  // half fluxes
+__device__ __forceinline__ void llf_flux_x2(const double (&qL)[NV], const double (&qR)[NV],
+                                            const Phys& p, double (&G)[NV]) {
+  double FL[NV], FR[NV], cL, cR;
   euler_flux<NV, D>(qL, p, FL, cL);
   euler_flux<NV, D>(qR, p, FR, cR);
-  const double halpha = 0.5 * ((cL >= cR) ? cL : cR);
+  const double alpha = (cL >= cR) ? cL : cR;
 #pragma unroll
-  for (int k = 0; k < NV; ++k) F[k] = fma(-halpha, qR[k] - qL[k], FL[k] + FR[k]);
+  for (int k = 0; k < NV; ++k) G[k] = fma(-alpha, qR[k] - qL[k], FL[k] + FR[k]);
 }
 
 // Monotonized-central limited slope (named in Sec. 4.2): 0 if ab <= 0, else
@@ -221,7 +231,7 @@ __device__ __forceinline__ double cfl_rate(const double (&q)[NV], const Phys& p,
   }
   const double P = Eos::pressure(p, rho, q[NV - 1], rho * v2);
   ok = fin && rho > 0.0 && P > 0.0;
-  const double c = sqrt_ctot(v2) + sound_over_xi(Eos::sound2(p, rho, P, ir), p);
+  const double c = sqrt_ctot(v2) + ctot_sound(p, rho, P, ir);
   return c * p.sum_inv_dx;
 }
 
