@@ -76,21 +76,46 @@ struct TileCfg {
   static constexpr int FY = NDIM >= 2 ? BX * (BY + 1) * BZ : 0;
   static constexpr int FZ = NDIM >= 3 ? BX * BY * (BZ + 1) : 0;
   static constexpr int FMAX = FX > FY ? (FX > FZ ? FX : FZ) : (FY > FZ ? FY : FZ);
-  static constexpr size_t SMEM = sizeof(double) * (size_t)NV * (SCELLS + FMAX) + 64 * sizeof(double);
+  // 1D/2D tiles keep each cell's MC slope along the current axis in shared
+  // memory (cells -1 .. B along that axis), computed once per cell instead
+  // of once per face side; 3D tiles recompute them (shared memory is short).
+  static constexpr bool SLOPES = NDIM <= 2;
+  static constexpr int EX0 = (BX + 2) * BY * BZ, EX1 = NDIM >= 2 ? BX * (BY + 2) * BZ : 0;
+  static constexpr int SEMAX = SLOPES ? (EX0 > EX1 ? EX0 : EX1) : 0;
+  static constexpr size_t SMEM = sizeof(double) * (size_t)NV * (SCELLS + FMAX + SEMAX) + 64 * sizeof(double);
 };
 
 // Faces along axis D of the tile: index space (BX + [D==0]) x (BY + [D==1]) x (BZ + [D==2]).
 template <int NDIM, int BX, int BY, int BZ, int NT, int D>
 __device__ __forceinline__ void face_pass(const double* __restrict__ su, double* __restrict__ sf,
-                                          const Phys& p, const Geom& g, int i0, int j0, int k0,
-                                          double (&dU)[TileCfg<NDIM, BX, BY, BZ, NT>::CPT][NDIM + 2]) {
+                                          double* __restrict__ ss, const Phys& p, const Geom& g, int i0, int j0,
+                                          int k0, double (&dU)[TileCfg<NDIM, BX, BY, BZ, NT>::CPT][NDIM + 2]) {
   using C = TileCfg<NDIM, BX, BY, BZ, NT>;
   constexpr int NV = C::NV;
   constexpr int EX = BX + (D == 0), EY = BY + (D == 1), EZ = BZ + (D == 2);
   constexpr int NF = EX * EY * EZ;
   constexpr int STRIDE = D == 0 ? 1 : (D == 1 ? C::SX : C::SX * C::SY);
+  // slope cells: tile coordinates -1 .. B along D, 0 .. B-1 across
+  constexpr int XX = BX + 2 * (D == 0), YY = BY + 2 * (D == 1), ZZ = BZ + 2 * (D == 2);
+  constexpr int NE = XX * YY * ZZ;
   const int nD = g.n[D];
   const int baseD = D == 0 ? i0 : (D == 1 ? j0 : k0);
+  if constexpr (C::SLOPES) {
+    for (int e = threadIdx.x; e < NE; e += NT) {
+      const int ex = e % XX;
+      const int t = e / XX;
+      const int ey = t % YY;
+      const int ez = t / YY;
+      const int s0 = (ez - (D == 2) + C::HZ) * C::SX * C::SY + (ey - (D == 1) + C::HY) * C::SX + (ex - (D == 0) + C::HX);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        const double* sv = su + v * C::SCELLS + s0;
+        const double um = sv[-STRIDE], u0 = sv[0], up = sv[STRIDE];
+        ss[v * C::SEMAX + e] = mc_slope(u0 - um, up - u0);
+      }
+    }
+    __syncthreads();
+  }
   for (int fid = threadIdx.x; fid < NF; fid += NT) {
     const int fx = fid % EX;
     const int t = fid / EX;
@@ -104,14 +129,26 @@ __device__ __forceinline__ void face_pass(const double* __restrict__ su, double*
     // shared-memory index of the cell right of the face
     const int s0 = (fz + C::HZ) * C::SX * C::SY + (fy + C::HY) * C::SX + (fx + C::HX);
     double qL[NV], qR[NV];
+    if constexpr (C::SLOPES) {
+      // slope index of the cell right of the face; the left one is STRIDE_E before
+      constexpr int STRIDE_E = D == 0 ? 1 : (D == 1 ? XX : XX * YY);
+      const int er = ((fz + (D == 2)) * YY + (fy + (D == 1))) * XX + (fx + (D == 0));
 #pragma unroll
-    for (int v = 0; v < NV; ++v) {
-      const double* sv = su + v * C::SCELLS + s0;
-      const double um2 = sv[-2 * STRIDE], um1 = sv[-STRIDE], u0 = sv[0], up1 = sv[STRIDE];
-      const double sl = mc_slope(um1 - um2, u0 - um1);
-      const double sr = mc_slope(u0 - um1, up1 - u0);
-      qL[v] = um1 + 0.5 * sl;
-      qR[v] = u0 - 0.5 * sr;
+      for (int v = 0; v < NV; ++v) {
+        const double* sv = su + v * C::SCELLS + s0;
+        qL[v] = fma(0.5, ss[v * C::SEMAX + er - STRIDE_E], sv[-STRIDE]);
+        qR[v] = fma(-0.5, ss[v * C::SEMAX + er], sv[0]);
+      }
+    } else {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        const double* sv = su + v * C::SCELLS + s0;
+        const double um2 = sv[-2 * STRIDE], um1 = sv[-STRIDE], u0 = sv[0], up1 = sv[STRIDE];
+        const double sl = mc_slope(um1 - um2, u0 - um1);
+        const double sr = mc_slope(u0 - um1, up1 - u0);
+        qL[v] = um1 + 0.5 * sl;
+        qR[v] = u0 - 0.5 * sr;
+      }
     }
     double F[NV];  // twice the face flux
     llf_flux_x2<NV, D>(qL, qR, p, F);
@@ -143,7 +180,8 @@ __global__ void __launch_bounds__(NT) stage_fp64_kernel(const StageArgs<double> 
   extern __shared__ double smem[];
   double* su = smem;
   double* sf = smem + NV * C::SCELLS;
-  double* sred = sf + NV * C::FMAX;
+  double* ss = sf + NV * C::FMAX;  // slopes (1D/2D tiles)
+  double* sred = ss + NV * C::SEMAX;
   const Geom& g = a.g;
   const Phys& p = a.p;
   const int i0 = blockIdx.x * BX, j0 = blockIdx.y * BY, k0 = blockIdx.z * BZ;
@@ -170,9 +208,9 @@ __global__ void __launch_bounds__(NT) stage_fp64_kernel(const StageArgs<double> 
   for (int c = 0; c < C::CPT; ++c)
 #pragma unroll
     for (int v = 0; v < NV; ++v) dU[c][v] = 0.0;
-  face_pass<NDIM, BX, BY, BZ, NT, 0>(su, sf, p, g, i0, j0, k0, dU);
-  if constexpr (NDIM >= 2) face_pass<NDIM, BX, BY, BZ, NT, 1>(su, sf, p, g, i0, j0, k0, dU);
-  if constexpr (NDIM >= 3) face_pass<NDIM, BX, BY, BZ, NT, 2>(su, sf, p, g, i0, j0, k0, dU);
+  face_pass<NDIM, BX, BY, BZ, NT, 0>(su, sf, ss, p, g, i0, j0, k0, dU);
+  if constexpr (NDIM >= 2) face_pass<NDIM, BX, BY, BZ, NT, 1>(su, sf, ss, p, g, i0, j0, k0, dU);
+  if constexpr (NDIM >= 3) face_pass<NDIM, BX, BY, BZ, NT, 2>(su, sf, ss, p, g, i0, j0, k0, dU);
 
   // 4. epilogue
   const double dt = a.dt_fixed > 0.0 ? a.dt_fixed : p.cfl / a.scal[a.slot];
