@@ -22,25 +22,32 @@
 // The derivatives are hand-derived reverse mode: each VJP recomputes its
 // forward values (holding the branches the forward pass took) and then runs
 // the chain rule backwards once, so a face costs about three flux
-// evaluations whatever the size of its stencil.
+// evaluations whatever the size of its stencil.  Divisions go through the
+// forward kernels' Newton-Raphson reciprocal and the square roots of c_tot
+// through their c_tot square root (float64 pipe economy; same readings).
 #include <cstring>
 #include <vector>
 
 #include "rsst_common.cuh"
 #include "rsst_internal.h"
+#include "rsst_math_fp64.cuh"
 
 namespace rsst {
 
 // |V| with a zero subgradient at V = 0.
-__device__ __forceinline__ double speed_of(double v2) { return v2 > 0.0 ? sqrt(v2) : 0.0; }
+__device__ __forceinline__ double speed_of(double v2) { return v2 > 0.0 ? sqrt_ctot(v2) : 0.0; }
 
 // MC branch (Sec. 4.2): 0 -> 0, 1 -> 2a, 2 -> 2b, 3 -> (a+b)/2; the
-// comparisons are the oracle's, so ties take the same branch.
+// decisions of the oracle's comparisons (2|a| <= 2|b| and 2|a| <= |a+b|/2,
+// then 2|b| <= |a+b|/2), taken on the integer pipe as in mc_slope.
 __device__ __forceinline__ int mc_branch(double a, double b) {
-  if (!(a * b > 0.0)) return 0;
-  const double aa = 2.0 * fabs(a), bb = 2.0 * fabs(b), cc = 0.5 * fabs(a + b);
-  if (aa <= bb && aa <= cc) return 1;
-  return bb <= cc ? 2 : 3;
+  const unsigned long long four = 1ull << 54;  // x4 in the shifted exponent field
+  const long long ia = __double_as_longlong(a), ib = __double_as_longlong(b);
+  const unsigned long long ua = (unsigned long long)ia << 1, ub = (unsigned long long)ib << 1;
+  if (!(((ia ^ ib) >= 0) && ua != 0 && ub != 0)) return 0;
+  const unsigned long long us = (unsigned long long)__double_as_longlong(a + b) << 1;
+  if (ua <= ub && ua + four <= us) return 1;
+  return ub + four <= us ? 2 : 3;
 }
 __device__ __forceinline__ double mc_value(int br, double a, double b) {
   return br == 0 ? 0.0 : (br == 1 ? 2.0 * a : (br == 2 ? 2.0 * b : 0.5 * (a + b)));
@@ -53,8 +60,8 @@ __device__ __forceinline__ void mc_reverse(int br, double ds, double& da, double
 
 // a/xi of a state (constant xi, or the C_max law, Eq. cx).
 __device__ __forceinline__ double sound_term(double a2, const Phys& p) {
-  if (p.use_cmax) return sqrt(a2 / sqrt(1.0 + (a2 * a2) * p.inv_cmax4));
-  return sqrt(a2) * p.inv_xi;
+  if (p.use_cmax) return sqrt(a2 * rcp_nr(sqrt(1.0 + (a2 * a2) * p.inv_cmax4)));
+  return sqrt_ctot(a2) * p.inv_xi;
 }
 
 // Euler flux along D and c_tot = |V| + a/xi of one state (Sec. 4.2).
@@ -62,14 +69,15 @@ template <int NV, int D>
 __device__ __forceinline__ void euler_flux_d(const double (&q)[NV], const Phys& p, double (&F)[NV], double& c) {
   constexpr int ND = NV - 2;
   const double rho = q[0];
+  const double ir = rcp_nr(rho);
   double v[ND];
   double v2 = 0.0;
   for (int e = 0; e < ND; ++e) {
-    v[e] = q[1 + e] / rho;
+    v[e] = q[1 + e] * ir;
     v2 += v[e] * v[e];
   }
   const double P = p.gm1 * (q[NV - 1] - 0.5 * (rho * v2));
-  c = speed_of(v2) + sound_term(p.gamma * P / rho, p);
+  c = speed_of(v2) + sound_term(p.gamma * P * ir, p);
   F[0] = q[1 + D];
   for (int e = 0; e < ND; ++e) F[1 + e] = (e == D) ? q[1 + e] * v[D] + P : q[1 + e] * v[D];
   F[NV - 1] = (q[NV - 1] + P) * v[D];
@@ -111,15 +119,16 @@ __device__ __forceinline__ double flux_vjp(const double (&q)[NV], const Phys& p,
                                            double (&dq)[NV]) {
   constexpr int ND = NV - 2;
   const double rho = q[0], E = q[NV - 1];
+  const double ir = rcp_nr(rho);
   double v[ND], dv[ND];
   double v2 = 0.0;
   for (int e = 0; e < ND; ++e) {
-    v[e] = q[1 + e] / rho;
+    v[e] = q[1 + e] * ir;
     v2 += v[e] * v[e];
     dv[e] = 0.0;
   }
   const double P = p.gm1 * (E - 0.5 * (rho * v2));
-  const double a2 = p.gamma * P / rho;
+  const double a2 = p.gamma * P * ir;
   double dP = dF[1 + D] + dF[NV - 1] * v[D], dv2 = 0.0, drho = 0.0, dE = dF[NV - 1] * v[D], dinv_xi = 0.0;
   dq[1 + D] += dF[0];
   for (int e = 0; e < ND; ++e) {
@@ -127,29 +136,29 @@ __device__ __forceinline__ double flux_vjp(const double (&q)[NV], const Phys& p,
     dv[D] += dF[1 + e] * q[1 + e];
   }
   dv[D] += dF[NV - 1] * (E + P);
-  if (v2 > 0.0) dv2 += dc * 0.5 / sqrt(v2);
+  if (v2 > 0.0) dv2 += dc * 0.5 * rcp_nr(sqrt_ctot(v2));
   double da2 = 0.0;
   if (p.use_cmax) {  // g = sqrt(u), u = a2 / t, t = sqrt(w), w = 1 + a2^2 / C^4
-    const double w = 1.0 + (a2 * a2) * p.inv_cmax4, t = sqrt(w), u = a2 / t;
+    const double w = 1.0 + (a2 * a2) * p.inv_cmax4, t = sqrt(w), it = rcp_nr(t), u = a2 * it;
     if (u > 0.0) {
-      const double du = dc / (2.0 * sqrt(u));
-      const double dt = -du * u / t;
-      da2 += du / t + (dt / (2.0 * t)) * 2.0 * a2 * p.inv_cmax4;
+      const double du = dc * 0.5 * rcp_nr(sqrt(u));
+      const double dt = -du * u * it;
+      da2 += du * it + dt * it * a2 * p.inv_cmax4;
     }
   } else {
-    const double s = sqrt(a2);
+    const double s = sqrt_ctot(a2);
     dinv_xi += dc * s;
-    if (a2 > 0.0) da2 += dc * p.inv_xi / (2.0 * s);
+    if (a2 > 0.0) da2 += dc * p.inv_xi * 0.5 * rcp_nr(s);
   }
-  dP += da2 * p.gamma / rho;
-  drho -= da2 * a2 / rho;
+  dP += da2 * p.gamma * ir;
+  drho -= da2 * a2 * ir;
   dE += dP * p.gm1;
   drho -= dP * p.gm1 * 0.5 * v2;
   dv2 -= dP * p.gm1 * 0.5 * rho;
   for (int e = 0; e < ND; ++e) {
     dv[e] += 2.0 * v[e] * dv2;
-    dq[1 + e] += dv[e] / rho;
-    drho -= dv[e] * v[e] / rho;
+    dq[1 + e] += dv[e] * ir;
+    drho -= dv[e] * v[e] * ir;
   }
   dq[0] += drho;
   dq[NV - 1] += dE;
@@ -211,10 +220,11 @@ __device__ __forceinline__ double rhs_vjp(const double (&q)[NV], const double (&
   }
   const int var = p.variant;
   if (var != RSST_EULER) {
+    const double ir = rcp_nr(rho);
     double v[ND], dv[ND];
     double v2 = 0.0, vdm = 0.0, mv = 0.0;
     for (int e = 0; e < ND; ++e) {
-      v[e] = q[1 + e] / rho;
+      v[e] = q[1 + e] * ir;
       v2 += v[e] * v[e];
       vdm += v[e] * dU[1 + e];
       mv += mu[1 + e] * v[e];
@@ -226,28 +236,29 @@ __device__ __forceinline__ double rhs_vjp(const double (&q)[NV], const double (&
     const bool pform = var == RSST_PVS || var == RSST_PMS || var == RSST_PD;
     const double sgn = (var == RSST_PVS || var == RSST_DVS) ? 1.0 : -1.0;
     const double H = P * p.inv_gm1 + P + sgn * kin;  // e + P +- rho|V|^2/2
-    double s, r0, rv, rE, ia2 = 0.0;
+    double s, r0, rv, rE, ia2 = 0.0, igP = 0.0;  // igP = 1/(gamma P)
     if (pform) {
       s = p.gm1 * (0.5 * (v2 * dU[0]) - vdm + dU[NV - 1]);
       if (var == RSST_PD) {
         r0 = 0.0; rv = 0.0; rE = p.inv_gm1;
       } else {
-        ia2 = rho / (p.gamma * P);
+        igP = rcp_nr(p.gamma * P);
+        ia2 = rho * igP;
         r0 = ia2;
         rv = var == RSST_PVS ? ia2 : 0.0;
-        rE = H * ia2 / rho;
+        rE = H * ia2 * ir;
       }
     } else {
       s = dU[0];
       r0 = 1.0;
       rv = var == RSST_DVS ? 1.0 : 0.0;
-      rE = H / rho;
+      rE = H * ir;
     }
     double a2 = 0.0, wc = 0.0, fc = p.f;
     if (p.use_cmax) {
-      a2 = p.gamma * P / rho;
+      a2 = p.gamma * P * ir;
       wc = 1.0 + (a2 * a2) * p.inv_cmax4;
-      fc = 1.0 - 1.0 / sqrt(wc);
+      fc = 1.0 - rcp_nr(sqrt(wc));
     }
     const double w = mu[0] * r0 + rv * mv + mu[NV - 1] * rE;
     const double ds = -fc * w, dw = -fc * s, dfc = -s * w;
@@ -267,21 +278,21 @@ __device__ __forceinline__ double rhs_vjp(const double (&q)[NV], const double (&
     if (var == RSST_PVS || var == RSST_PMS) {
       double dia2 = dw * mu[0] + (var == RSST_PVS ? dw * mv : 0.0);
       const double drE = dw * mu[NV - 1];
-      dH = drE * ia2 / rho;
-      dia2 += drE * H / rho;
-      drho -= drE * rE / rho;
-      drho += dia2 / (p.gamma * P);
-      dP -= dia2 * ia2 / P;
+      dH = drE * ia2 * ir;
+      dia2 += drE * H * ir;
+      drho -= drE * rE * ir;
+      drho += dia2 * igP;
+      dP -= dia2 * ia2 * (p.gamma * igP);  // ia2 / P
     } else if (var == RSST_DVS || var == RSST_DMS) {
-      dH = dw * mu[NV - 1] / rho;
-      drho -= dw * mu[NV - 1] * rE / rho;
+      dH = dw * mu[NV - 1] * ir;
+      drho -= dw * mu[NV - 1] * rE * ir;
     }
     dP += dH * (p.inv_gm1 + 1.0);
     const double dkin = sgn * dH;
     if (p.use_cmax) {
-      const double da2 = dfc * p.inv_cmax4 * a2 / (wc * sqrt(wc));
-      dP += da2 * p.gamma / rho;
-      drho -= da2 * a2 / rho;
+      const double da2 = dfc * p.inv_cmax4 * a2 * rcp_nr(wc * sqrt(wc));
+      dP += da2 * p.gamma * ir;
+      drho -= da2 * a2 * ir;
     } else {
       dfc_total = dfc;
     }
@@ -292,8 +303,8 @@ __device__ __forceinline__ double rhs_vjp(const double (&q)[NV], const double (&
     dv2 -= dP * p.gm1 * 0.5 * rho;
     for (int e = 0; e < ND; ++e) {
       dv[e] += 2.0 * v[e] * dv2;
-      dq[1 + e] += dv[e] / rho;
-      drho -= dv[e] * v[e] / rho;
+      dq[1 + e] += dv[e] * ir;
+      drho -= dv[e] * v[e] * ir;
     }
     dq[0] += drho;
   }
