@@ -8,9 +8,9 @@
 // One stage is out = a * base + b * (in + dt L(in)).  Its adjoint needs the
 // vector-Jacobian product mu^T dL/d(in) (mu = b dt lambda_out) and
 // mu^T dL/dxi:
-//   adj_cell: per interior cell, recompute the Euler tendency dU from the
-//     2 * ndim face fluxes around it, then nu = mu^T dC/d(dU) and the
-//     pointwise part mu^T d(C + force)/dq (C = reduced tendency, Sec. 3.2 /
+//   adj_cell: per interior cell, with the Euler tendency dU that the forward
+//     kernel wrote while the segment was recomputed, nu = mu^T dC/d(dU) and
+//     the pointwise part mu^T d(C + force)/dq (C = reduced tendency, Sec. 3.2 /
 //     App. A; force of App. B), and the xi partial;
 //   adj_face: per face, phi = (nu_right - nu_left)/dx, then phi^T dF/dU_k for
 //     the four stencil cells k of the face (MC slopes, face states, LLF flux
@@ -96,19 +96,6 @@ __device__ __forceinline__ void face_states(const double (&s)[4][NV], double (&q
     qL[v] = s[1][v] + 0.5 * mc_value(bL[v], aL, dL);
     qR[v] = s[2][v] - 0.5 * mc_value(bR[v], aR, dR);
   }
-}
-
-// LLF flux F = (FL + FR)/2 - alpha (qR - qL)/2, alpha = max(cL, cR) with ties
-// to the left state (Sec. 4.2).
-template <int NV, int D>
-__device__ __forceinline__ void face_flux(const double (&s)[4][NV], const Phys& p, double (&F)[NV]) {
-  double qL[NV], qR[NV], FL[NV], FR[NV], cL, cR;
-  int bL[NV], bR[NV];
-  face_states<NV>(s, qL, qR, bL, bR);
-  euler_flux_d<NV, D>(qL, p, FL, cL);
-  euler_flux_d<NV, D>(qR, p, FR, cR);
-  const double alpha = cL >= cR ? cL : cR;
-  for (int v = 0; v < NV; ++v) F[v] = 0.5 * (FL[v] + FR[v]) - 0.5 * (alpha * (qR[v] - qL[v]));
 }
 
 // Reverse of euler_flux_d at q: adds dF^T dF/dq + dc dc/dq to dq and returns
@@ -319,6 +306,7 @@ __device__ __forceinline__ double rhs_vjp(const double (&q)[NV], const double (&
 
 struct AdjArgs {
   const double* U;   // stage input, padded
+  const double* dU;  // its Euler tendency, padded (written by the forward kernel on recompute)
   const double* mu;  // b dt lambda_out, padded (interior used)
   double* nu;        // padded, interior written (ghosts stay zero)
   double* lam;       // padded output: pointwise part written to the interior
@@ -354,7 +342,6 @@ __device__ __forceinline__ void load_stencil(const AdjArgs& a, const int (&c)[3]
 
 template <int NV>
 __global__ void __launch_bounds__(128) adj_cell_kernel(AdjArgs a) {
-  constexpr int ND = NV - 2;
   __shared__ double sh[128];
   const Geom& g = a.g;
   const Phys& p = a.p;
@@ -367,20 +354,7 @@ __global__ void __launch_bounds__(128) adj_cell_kernel(AdjArgs a) {
     for (int v = 0; v < NV; ++v) {
       q[v] = a.U[v * g.fstride + o];
       mu[v] = a.mu[v * g.fstride + o];
-      dU[v] = 0.0;
-    }
-    // Euler tendency from the 2 * ndim faces
-    for (int d = 0; d < ND; ++d) {
-      for (int side = 0; side < 2; ++side) {
-        int cf[3] = {c[0], c[1], c[2]};
-        cf[d] += side;  // face cf[d] - 1/2
-        double s[4][NV], F[NV];
-        if (d == 0) { load_stencil<NV, 0>(a, cf, s); face_flux<NV, 0>(s, p, F); }
-        if (d == 1) { if constexpr (ND >= 2) { load_stencil<NV, 1>(a, cf, s); face_flux<NV, 1>(s, p, F); } }
-        if (d == 2) { if constexpr (ND >= 3) { load_stencil<NV, 2>(a, cf, s); face_flux<NV, 2>(s, p, F); } }
-        const double sg = side == 0 ? 1.0 : -1.0;
-        for (int v = 0; v < NV; ++v) dU[v] += sg * F[v] * p.inv_dx[d];
-      }
+      dU[v] = a.dU[v * g.fstride + o];
     }
     // nu = mu^T dL/d(dU), pointwise mu^T dL/dq, xi partial (f = 1 - 1/xi^2)
     double nu[NV], dq[NV];
@@ -586,6 +560,7 @@ struct AdjState {
   int nsteps = 0, every = 0, nseg = 0;
   std::vector<double*> ckpt;   // padded states at steps 0, every, 2 every, ...
   double* stages = nullptr;    // recompute storage: 2 * every padded states
+  double* dUs = nullptr;       // their Euler tendencies (same layout)
   double* lamA = nullptr;      // padded work arrays
   double* lamB = nullptr;
   double* lamC = nullptr;
@@ -605,6 +580,7 @@ void rsst_adjoint_free(rsst_handle* h) {
   if (!s) return;
   for (double* c : s->ckpt) cudaFree(c);
   cudaFree(s->stages);
+  cudaFree(s->dUs);
   cudaFree(s->lamA);
   cudaFree(s->lamB);
   cudaFree(s->lamC);
@@ -656,6 +632,7 @@ extern "C" int rsst_adjoint_record(rsst_handle* h, double dt, int nsteps, int ev
   s->part_len = blocks_for(g.ncells) + 3 * blocks_for(faces) + 8;
   const int nv = g.ndim + 2;
   bool ok = cudaMalloc((void**)&s->stages, 2 * (size_t)every * sb) == cudaSuccess &&
+            cudaMalloc((void**)&s->dUs, 2 * (size_t)every * sb) == cudaSuccess &&
             cudaMalloc((void**)&s->lamA, sb) == cudaSuccess && cudaMalloc((void**)&s->lamB, sb) == cudaSuccess &&
             cudaMalloc((void**)&s->lamC, sb) == cudaSuccess &&
             cudaMalloc((void**)&s->mu, sb) == cudaSuccess && cudaMalloc((void**)&s->nu, sb) == cudaSuccess &&
@@ -696,7 +673,8 @@ extern "C" int rsst_adjoint_segments(rsst_handle* h, int32_t* nseg) {
 // in: the stage input state; b: coefficient of (in + dt L(in)).
 // Writes lam_in = b lam_out + (b dt lam_out)^T dL/d(in) into `res` (padded,
 // interior, ghosts folded) and adds the xi partials to s->dxi.
-static int stage_vjp(rsst_handle* h, AdjState* s, const double* in, const double* lam_out, double b, double* res) {
+static int stage_vjp(rsst_handle* h, AdjState* s, const double* in, const double* dU, const double* lam_out, double b,
+                     double* res) {
   const Geom& g = h->g;
   const int nv = g.ndim + 2;
   cudaStream_t st = h->stream;
@@ -709,6 +687,7 @@ static int stage_vjp(rsst_handle* h, AdjState* s, const double* in, const double
   AdjArgs a;
   memset(&a, 0, sizeof a);
   a.U = in;
+  a.dU = dU;
   a.mu = s->mu;
   a.nu = s->nu;
   a.lam = res;
@@ -783,7 +762,10 @@ extern "C" int rsst_adjoint_step(rsst_handle* h, int32_t seg, double* lam, doubl
   cudaMemcpyAsync(h->buf[0], s->ckpt[seg], sb, cudaMemcpyDeviceToDevice, st);
   for (int i = 0; i < k && rc == RSST_OK; ++i) {
     cudaMemcpyAsync(s->stages + (2 * i) * fe, h->buf[0], sb, cudaMemcpyDeviceToDevice, st);
+    h->rec_dU[0] = s->dUs + (2 * i) * fe;      // the forward kernels also write each stage's Euler tendency
+    h->rec_dU[1] = s->dUs + (2 * i + 1) * fe;
     rc = rsst_handle_steps(h, s->dt, 1);
+    h->rec_dU[0] = h->rec_dU[1] = nullptr;
     // buf[1] still holds U* of this step
     cudaMemcpyAsync(s->stages + (2 * i + 1) * fe, h->buf[1], sb, cudaMemcpyDeviceToDevice, st);
   }
@@ -800,10 +782,10 @@ extern "C" int rsst_adjoint_step(rsst_handle* h, int32_t seg, double* lam, doubl
       const double* Un = s->stages + (2 * i) * fe;
       const double* Us = s->stages + (2 * i + 1) * fe;
       // stage 2: U^{n+1} = 1/2 U^n + 1/2 (U* + dt L(U*)):  lamB = lambda_*
-      rc = stage_vjp(h, s, Us, s->lamA, 0.5, s->lamB);
+      rc = stage_vjp(h, s, Us, s->dUs + (2 * i + 1) * fe, s->lamA, 0.5, s->lamB);
       if (rc) break;
       // stage 1: U* = U^n + dt L(U^n):  lamC = lambda_* dU*/dU^n
-      rc = stage_vjp(h, s, Un, s->lamB, 1.0, s->lamC);
+      rc = stage_vjp(h, s, Un, s->dUs + (2 * i) * fe, s->lamB, 1.0, s->lamC);
       if (rc) break;
       // lambda^n = 1/2 lambda^{n+1} + lamC
       axpby_kernel<<<blocks_for(g.ncells), 128, 0, st>>>(s->lamA, s->lamA, 0.5, s->lamC, 1.0, g, nv);

@@ -358,6 +358,7 @@ static int plain_steps(rsst_handle* h, double dt, int nsteps, cudaStream_t st) {
     a.in = U;
     a.base = nullptr;
     a.out = Us;
+    a.dU_out = h->rec_dU[0];
     if constexpr (std::is_same<T, double>::value) RC_TRY(rsst_launch_stage_fp64(a, st));
     else if constexpr (std::is_same<T, float2>::value) RC_TRY(rsst_launch_stage_df(a, st));
     else if (h->use_tma2d) RC_TRY(rsst_launch_stage2d_tma(&h->tmap[0], a, st));
@@ -367,6 +368,7 @@ static int plain_steps(rsst_handle* h, double dt, int nsteps, cudaStream_t st) {
     a.in = Us;
     a.base = U;
     a.out = U;
+    a.dU_out = h->rec_dU[1];
     if constexpr (std::is_same<T, double>::value) RC_TRY(rsst_launch_stage_fp64(a, st));
     else if constexpr (std::is_same<T, float2>::value) RC_TRY(rsst_launch_stage_df(a, st));
     else if (h->use_tma2d) RC_TRY(rsst_launch_stage2d_tma(&h->tmap[1], a, st));
@@ -421,7 +423,7 @@ static int build_graph(rsst_handle* h, double dt) {
 template <typename T>
 static int run_steps(rsst_handle* h, double dt, int nsteps) {
   const int K = h->graph_steps;
-  if (K > 0 && nsteps >= K) {
+  if (K > 0 && nsteps >= K && !h->rec_dU[0] && !h->rec_dU[1]) {
     if (!h->graph_warm) {  // first launch sets the kernels' attributes outside any capture
       RC_TRY(plain_steps<T>(h, dt, 1, h->stream));
       h->graph_warm = 1;

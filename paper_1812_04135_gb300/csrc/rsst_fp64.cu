@@ -238,6 +238,11 @@ __global__ void __launch_bounds__(NT) stage_fp64_kernel(const StageArgs<double> 
       q[v] = su[v * C::SCELLS + s0];
       L[v] = dU[c][v];
     }
+    if (a.dU_out) {
+      const int64_t o = pidx(g, i, j, k);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) a.dU_out[v * g.fstride + o] = L[v];
+    }
     rsst_rhs<NV>(q, L, p);
     if (a.stage == 1) {
 #pragma unroll

@@ -94,6 +94,8 @@ struct StageArgs {
   PhysF pf;         // float32 constants (float32 kernels)
   const float* tab; // background tables [TB_COUNT][tab_len] (float32 mode), or null
   int tab_len;
+  double* dU_out;   // float64 kernels: if set, the Euler tendency of each interior cell
+                    // (padded layout) is written here too (adjoint recompute)
 };
 
 // Host-side launchers (defined in the .cu files).
@@ -160,6 +162,7 @@ struct rsst_handle {
   cudaGraphExec_t gexec[2];
   int gvalid[2];
   double gdt[2];            // the dt each graph was captured with
+  double* rec_dU[2];        // float64 plain steps: Euler tendency of stage 1 / 2 written here if set
 };
 
 void rsst_adjoint_free(rsst_handle* h);
