@@ -7,8 +7,8 @@ reverse-mode differentiation (torch.autograd) of the plain oracle step in
 (MC limiter branch, LLF max with ties to the left state, |V| with a zero
 subgradient at V = 0).
 
-Conventions (the paper has no adjoint; these readings are stated in
-the design doc): dt is fixed for the whole run and not differentiated; the
+Conventions (the paper has no adjoint, so these are this project's
+readings): dt is fixed for the whole run and not differentiated; the
 functional is the final kinetic energy J = sum |m|^2/(2 rho) dV; gradients are
 taken with respect to every component of the initial conserved state (the
 density gradient at fixed m and E is component 0) and with respect to xi.

@@ -21,7 +21,7 @@ technique for low Mach number flows with large density variations"
   with c_tot = |V| + a/xi, second-order SSP Runge-Kutta, CFL number 0.4 with
   c_tot, in the order of the eight implementation steps listed there.
 
-Readings where the paper is silent (each also listed in the design doc):
+Readings where the paper is silent:
 * MC limiter (only named in Sec. 4.2): MC(a, b) = 0 if a*b <= 0, else the
   one of 2a, 2b, (a+b)/2 with the smallest magnitude; ties go to the first
   in that order.

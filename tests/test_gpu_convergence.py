@@ -89,7 +89,7 @@ def test_entropy_and_shear_second_order_pressure_reduced(table, var):
 def test_entropy_and_shear_converge_density_reduced(table, var):
     """S and V_perp converge in the density-reduced forms too (average order
     over 32 -> 256 above 1.5); their last doubling degrades towards first
-    order, where the paper reports second order (recorded in the design doc)."""
+    order, where the paper reports second order."""
     for field in ("S", "Vperp"):
         avg = math.log2(table[var][32][field] / table[var][256][field]) / 3.0
         assert avg > 1.5, (var, field, avg)
