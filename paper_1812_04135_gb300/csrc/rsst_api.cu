@@ -40,6 +40,8 @@ extern "C" const char* rsst_last_error(void) { return g_err; }
 
 
 
+void rsst_stage2d_box(int* box_x, int* box_y);  // rsst_fp32_2d.cu
+
 static int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 
 // cuTensorMapEncodeTiled from the driver, looked up once (no link-time libcuda).
@@ -259,7 +261,9 @@ extern "C" int rsst_init(rsst_handle** out, const rsst_config* cfg, void* stream
   if (cfg->precision == RSST_FP32_PERT && cfg->ndim == 2 && (cfg->vertical == -1 || cfg->vertical == 1)) {
     h->use_tma2d = 1;
     for (int b = 0; b < 2; ++b) {
-      rc = make_tmap_2d(&h->tmap[b], h->buf[b], h->g, nv, 72, 36);
+      int bx, by;
+      rsst_stage2d_box(&bx, &by);
+      rc = make_tmap_2d(&h->tmap[b], h->buf[b], h->g, nv, bx, by);
       if (rc != RSST_OK) goto fail;
     }
   }

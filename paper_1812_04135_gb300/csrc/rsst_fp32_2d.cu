@@ -1,8 +1,8 @@
 // Float32 perturbation stage kernel for 2D grids, TMA-staged.
 //
-// One tile = 64 x 32 cells, 256 threads.
+// One tile = 64 x 24 cells, 192 threads (three CTAs per SM).
 //   1. One thread issues a single cp.async.bulk.tensor load of the tile with
-//      its halo for all four fields (box 72 x 36 x 4 of the padded state, the
+//      its halo for all four fields (box 72 x 28 x 4 of the padded state, the
 //      x origin rounded down to a 16-byte boundary, out-of-range parts zero
 //      filled); the others stage the background table rows of the tile.
 //   2. x faces, one per thread in turn (lanes along x, conflict-free), LLF
@@ -20,7 +20,7 @@
 namespace rsst {
 
 template <int VERT>
-__global__ void __launch_bounds__(T2::NT, 2) stage2d_tma_kernel(const __grid_constant__ CUtensorMap tin,
+__global__ void __launch_bounds__(T2::NT, 3) stage2d_tma_kernel(const __grid_constant__ CUtensorMap tin,
                                                                  const StageArgs<float> a) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   TileRun r;
@@ -63,6 +63,12 @@ __global__ void __launch_bounds__(T2::NT, 2) stage2d_tma_kernel(const __grid_con
 }  // namespace rsst
 
 using namespace rsst;
+
+// TMA box of the single-run tile (halo included), for the tensor maps.
+void rsst_stage2d_box(int* box_x, int* box_y) {
+  *box_x = T2::SXP;
+  *box_y = T2::SYP;
+}
 
 int rsst_launch_stage2d_tma(const CUtensorMap* tin, const StageArgs<float>& a, cudaStream_t s) {
   const int vert = a.tab ? a.p.vertical : -1;
