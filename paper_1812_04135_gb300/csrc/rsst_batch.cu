@@ -92,9 +92,10 @@ using TC0 = T2Cfg<64, 32, 8>;
 using TC1 = T2Cfg<32, 32, 8>;
 using TC2 = T2Cfg<64, 16, 4>;
 using TC3 = T2Cfg<128, 16, 8>;
-constexpr int NCAND = 4;
-static const int CAND_BX[NCAND] = {64, 32, 64, 128};
-static const int CAND_BY[NCAND] = {32, 32, 16, 16};
+using TC4 = T2Cfg<64, 24, 8>;
+constexpr int NCAND = 5;
+static const int CAND_BX[NCAND] = {64, 32, 64, 128, 64};
+static const int CAND_BY[NCAND] = {32, 32, 16, 16, 24};
 
 }  // namespace rsst
 
@@ -137,7 +138,8 @@ static void* cand_kernel(int c, int* nt, size_t* smem) {
     case 0: *nt = TC0::NT; *smem = TC0::smem_bytes(); return kernel_of<TC0>();
     case 1: *nt = TC1::NT; *smem = TC1::smem_bytes(); return kernel_of<TC1>();
     case 2: *nt = TC2::NT; *smem = TC2::smem_bytes(); return kernel_of<TC2>();
-    default: *nt = TC3::NT; *smem = TC3::smem_bytes(); return kernel_of<TC3>();
+    case 3: *nt = TC3::NT; *smem = TC3::smem_bytes(); return kernel_of<TC3>();
+    default: *nt = TC4::NT; *smem = TC4::smem_bytes(); return kernel_of<TC4>();
   }
 }
 
@@ -216,7 +218,8 @@ static int launch_stage(rsst_batch* b, int stage, int slot) {
     case 0: batch_stage_kernel<TC0><<<b->grid, nt, smem, b->stream>>>(b->d_runs, b->d_tile_begin, b->nruns, b->total_tiles, stage, slot); break;
     case 1: batch_stage_kernel<TC1><<<b->grid, nt, smem, b->stream>>>(b->d_runs, b->d_tile_begin, b->nruns, b->total_tiles, stage, slot); break;
     case 2: batch_stage_kernel<TC2><<<b->grid, nt, smem, b->stream>>>(b->d_runs, b->d_tile_begin, b->nruns, b->total_tiles, stage, slot); break;
-    default: batch_stage_kernel<TC3><<<b->grid, nt, smem, b->stream>>>(b->d_runs, b->d_tile_begin, b->nruns, b->total_tiles, stage, slot); break;
+    case 3: batch_stage_kernel<TC3><<<b->grid, nt, smem, b->stream>>>(b->d_runs, b->d_tile_begin, b->nruns, b->total_tiles, stage, slot); break;
+    default: batch_stage_kernel<TC4><<<b->grid, nt, smem, b->stream>>>(b->d_runs, b->d_tile_begin, b->nruns, b->total_tiles, stage, slot); break;
   }
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
