@@ -430,7 +430,7 @@ int rsst_launch_stage_fp64(const StageArgs<double>& a, cudaStream_t s) {
     case 1:  // short lines: 16-cell tiles (17 faces, one per thread of a warp) spread the float64 work over SMs
       if (a.g.n[0] <= RSST_SMALL_1D) return launch_stage<1, 16, 1, 1, 32>(a, s);
       return launch_stage<1, 256, 1, 1, 256>(a, s);
-    case 2: return launch_stage<2, 32, 8, 1, 256>(a, s);
+    case 2: return launch_stage<2, 32, 8, 1, 288>(a, s);  // 9 warps: every face and slope pass in one round
     case 3: return launch_stage<3, 16, 8, 4, 256>(a, s);
   }
   rsst_set_error("ndim must be 1, 2 or 3");
