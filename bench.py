@@ -40,6 +40,14 @@ L2_FLUSH_BYTES = 256 << 20
 # force + RK ~40 (+3 div, 2 sqrt); div and sqrt counted as one operation each.
 FP64_FLOPS_PER_CELL_STAGE_2D = 2 * (122 + 6) + 8 + 45
 
+# float64 operations of the discrete adjoint per primal cell-stage (2D, PVS,
+# constant xi), counted the same way from the reverse-mode code: the forward
+# record and the segment recompute are one forward stage each (309); the
+# stage VJP is 2 faces x 334 (face states 48, two c_tot evaluations 32, LLF
+# reverse 36, two flux reverses 148, MC reverse 64, phi 8, xi 2) + the
+# reduced-tendency reverse 133 + the mu scaling, gather and combines 52.
+ADJ_FLOPS_PER_CELL_STAGE_2D = 309 + 309 + (2 * 334 + 133 + 52)
+
 
 def _sources_sha(files):
     import hashlib
@@ -366,6 +374,85 @@ def run_batched(args, world, rank, local):
     print(json.dumps(line), flush=True)
 
 
+def run_adjoint(args, world, rank, local):
+    """Discrete adjoint of the 2D 256^2 float64 stratified box (contrast 20,
+    xi = 20): forward record of 400 steps with a checkpoint every 20, then the
+    reverse sweep for dJ/dU0 and dJ/dxi of the final kinetic energy.  One
+    bench step is one such full gradient; the value counts the primal
+    cell-stages (cells x 2 x 400) per second of forward + reverse."""
+    from paper_1812_04135_gb300 import inputs, rsst
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w = inputs.polytrope_2d(256, 256, xi=20.0, contrast=20.0, amp=1e-3)
+    cells, nsteps, every = 256 * 256, 400, 20
+    stream = torch.cuda.current_stream(dev)
+    s = rsst.Solver(w, "fp64", stream=stream)
+    U0 = torch.from_numpy(w["U"]).to(dev)
+    s.set_state(U0)
+    dt = s.dt()
+    g = torch.empty(tuple(U0.shape), dtype=torch.float64, device=dev)
+
+    def gradient(src, on_host=False):
+        rsst.rsst_set_state(s.h, src, on_host=on_host)
+        rsst.rsst_adjoint_record(s.h, dt, nsteps, every)
+        rsst.rsst_kinetic_energy(s.h, g)
+        dxi = 0.0
+        for seg in reversed(range(rsst.rsst_adjoint_segments(s.h))):
+            dxi += rsst.rsst_adjoint_step(s.h, seg, g)
+        return dxi
+
+    for _ in range(args.warmup):
+        gradient(U0)
+    torch.cuda.synchronize()
+    l0 = s.launches()
+    _barrier(world)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            dxi = gradient(U0)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    _barrier(world)
+    launches = s.launches() - l0
+    t_max = _max_over_ranks(e0.elapsed_time(e1) / 1e3, world)
+    value = cells * 2 * nsteps * args.steps * world / t_max
+    # end to end: the initial state from pinned host memory, the gradient back to it
+    host_in = torch.from_numpy(w["U"]).pin_memory()
+    host_out = torch.empty_like(host_in).pin_memory()
+    torch.cuda.synchronize()
+    w0 = time.perf_counter()
+    for _ in range(args.steps):
+        gradient(host_in, on_host=True)
+        host_out.copy_(g, non_blocking=True)
+        torch.cuda.synchronize()
+    e_el = _max_over_ranks(time.perf_counter() - w0, world)
+    s.close()
+    if rank != 0:
+        return
+    c = clk.summary()
+    sm_mhz = c["sm_mhz"] or 1900.0
+    flops = ADJ_FLOPS_PER_CELL_STAGE_2D * cells * 2 * nsteps * args.steps / t_max
+    peak_tf = fp64_peak_tflops(sm_mhz)
+    line = {"metric": METRIC, "value": value, "unit": UNIT + " (primal cell-stages of forward record + reverse sweep)",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": t_max / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "adjoint: 2D 256x256 stratified box, contrast 20, xi=20, FP64 PVS, 400 steps, "
+                                   "checkpoint every 20, gradient of the final kinetic energy w.r.t. U0 and xi",
+                       "cells": cells, "steps_per_gradient": nsteps, "checkpoint_every": every,
+                       "l2": "working set (checkpoints, recompute storage) larger than L2",
+                       "parallelism": f"replicas x{args.gpus}"},
+            "roofline": {"bound": "alu", "achieved": flops / 1e12, "peak": peak_tf, "unit": "TFLOP/s",
+                         "frac": flops / 1e12 / peak_tf, "traffic": None,
+                         "scope": "whole gradient (forward, recompute and VJP kernels), algorithmic float64 count",
+                         "peak_source": f"float64: 152 SMs x 2 DFMA/clk x 2 flop x {sm_mhz:.0f} MHz"},
+            "e2e": {"value": cells * 2 * nsteps * args.steps * world / e_el, "unit": UNIT,
+                    "h2d_bytes_per_step": host_in.numel() * 8, "d2h_bytes_per_step": host_out.numel() * 8},
+            "gpu_launches": launches, "clocks": c, "dJ_dxi": dxi}
+    print(json.dumps(line), flush=True)
+
+
 def cpu_baseline(w, seconds: float):
     """The oracle as it stands on the host cores: full-grid steps until ~``seconds``."""
     from oracle import rsst_oracle as ro
@@ -386,8 +473,72 @@ def cpu_baseline(w, seconds: float):
                       f"({el:.1f} s, torch CPU float64)"}
 
 
+def run_reference_adjoint(args):
+    """The oracle's discrete adjoint (torch autograd of the oracle step) on
+    the 256^2 adjoint workload: each step is a 2-step gradient with a
+    checkpoint every step, a bounded sample of the 400-step gradient."""
+    from oracle import adjoint as adj
+    from oracle import rsst_oracle as ro
+    from oracle.workload import problem_from
+    from paper_1812_04135_gb300 import inputs
+    w = inputs.polytrope_2d(256, 256, xi=20.0, contrast=20.0, amp=1e-3)
+    prob, U = problem_from(w)
+    dt = ro.cfl_dt(U, prob)
+    cells, k = 256 * 256, 2
+    for _ in range(args.warmup):
+        adj.adjoint_run(U, prob, k, dt, 1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        adj.adjoint_run(U, prob, k, dt, 1)
+    el = time.perf_counter() - t0
+    v = cells * 2 * k * args.steps / el
+    cfg = {"workload": "adjoint: 2D 256x256 stratified box, contrast 20, xi=20, FP64 PVS; oracle sample of "
+                       f"{k}-step gradients", "cells": cells}
+    return v, el, cfg, f"{args.steps} gradients of {k} steps (checkpoint every step) after {args.warmup} warm-up"
+
+
+def run_reference_batched(args):
+    """The oracle on the batched workload: each step advances 4 of the 64 runs
+    by one SSP-RK2 step (rotating through the list), a bounded sample."""
+    from oracle import rsst_oracle as ro
+    from oracle.workload import problem_from
+    from paper_1812_04135_gb300 import inputs
+    ws = inputs.batched_runs(count=64, seed=4)
+    probs = [problem_from(w) for w in ws]
+    state = [U for _, U in probs]
+    done = 0
+
+    def one(i):
+        prob = probs[i][0]
+        state[i] = ro.ssp_rk2_step(state[i], ro.cfl_dt(state[i], prob), prob)
+        return int(np.prod(ws[i]["n"]))
+
+    for j in range(args.warmup):
+        one(j % 64)
+    t0 = time.perf_counter()
+    for j in range(args.steps):
+        for r in range(4):
+            done += one((4 * j + r) % 64)
+    el = time.perf_counter() - t0
+    v = done * 2 / el
+    cfg = {"workload": "batched: 64 independent 2D shear layers, N in {128..1024}^2; oracle sample of 4 runs per step",
+           "cells": sum(int(np.prod(w["n"])) for w in ws)}
+    return v, el, cfg, f"{args.steps} steps of 4 runs each (rotating through the 64) after {args.warmup} warm-up"
+
+
 def run_reference(args, world, rank):
     if rank != 0:
+        return
+    if args.workload in ("adjoint", "batched"):
+        v, el, cfg, sample = (run_reference_adjoint if args.workload == "adjoint" else run_reference_batched)(args)
+        line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic", "config": cfg,
+                "cpu_baseline": {"value": v, "unit": UNIT, "cores": torch.get_num_threads(), "kind": "oracle",
+                                 "sample": sample},
+                "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
         return
     w = workload(args)
     from oracle import rsst_oracle as ro
@@ -525,7 +676,7 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--n", type=int, default=512)
     ap.add_argument("--variant", default="pvs")
-    ap.add_argument("--workload", default="shear2d", choices=["shear2d", "polytrope3d", "batched"])
+    ap.add_argument("--workload", default="shear2d", choices=["shear2d", "polytrope3d", "batched", "adjoint"])
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32_pert", "fp64_df"])
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -536,6 +687,8 @@ def main():
         run_reference(args, world, rank)
     elif args.workload == "batched":
         run_batched(args, world, rank, local)
+    elif args.workload == "adjoint":
+        run_adjoint(args, world, rank, local)
     else:
         run_gpu(args, world, rank, local)
     if world > 1:
