@@ -59,6 +59,10 @@ def _sources_sha(files):
 
 
 def _traffic_for(args, w):
+    return _traffic_key(f"{args.workload}:{args.precision}:{w['n'][0]}")
+
+
+def _traffic_key(key):
     """DRAM bytes per launch of the dominant kernel from the committed ncu
     summary (profiles/traffic.json), only if its sources are unchanged."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
@@ -66,7 +70,6 @@ def _traffic_for(args, w):
         return None
     with open(p) as f:
         table = json.load(f)
-    key = f"{args.workload}:{args.precision}:{w['n'][0]}"
     e = table.get(key)
     if not e or _sources_sha(e["sources"]) != e["sources_sha"]:
         return None
@@ -366,7 +369,8 @@ def run_batched(args, world, rank, local):
                        "cells": cells, "tile_shape": shape, "autotune_choice": choice,
                        "l2": "inputs larger than L2 (0.64 GB of state)", "parallelism": f"replicas x{args.gpus}"},
             "roofline": {"bound": "hbm", "achieved": hbm, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                         "frac": hbm / peaks["hbm_gbs"], "traffic": None, "peak_source": src},
+                         "frac": hbm / peaks["hbm_gbs"], "traffic": _traffic_key(f"batched:fp32_pert:{len(ws)}"),
+                         "peak_source": src},
             "looped_single_run": {"value": cells * 2 * args.steps / t_loop, "ms_per_step": t_loop / args.steps * 1e3},
             "e2e": {"value": cells * 2 * args.steps * world / e_el, "unit": UNIT,
                     "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
