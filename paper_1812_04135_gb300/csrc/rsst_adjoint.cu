@@ -11,7 +11,8 @@
 //   adj_cell: per interior cell, with the Euler tendency dU that the forward
 //     kernel wrote while the segment was recomputed, nu = mu^T dC/d(dU) and
 //     the pointwise part mu^T d(C + force)/dq (C = reduced tendency, Sec. 3.2 /
-//     App. A; force of App. B), and the xi partial;
+//     App. A; force of App. B) plus the identity part b lambda_out, and the
+//     xi partial;
 //   adj_face: per face, phi = (nu_right - nu_left)/dx, then phi^T dF/dU_k for
 //     the four stencil cells k of the face (MC slopes, face states, LLF flux
 //     of Sec. 4.2) and the xi partial;
@@ -307,7 +308,9 @@ __device__ __forceinline__ double rhs_vjp(const double (&q)[NV], const double (&
 struct AdjArgs {
   const double* U;   // stage input, padded
   const double* dU;  // its Euler tendency, padded (written by the forward kernel on recompute)
-  const double* mu;  // b dt lambda_out, padded (interior used)
+  const double* lam_out;  // lambda of the stage output, padded (interior used)
+  double mu_scale;        // mu = mu_scale * lambda_out = b dt lambda_out
+  double id_scale;        // the stage's identity part adds id_scale * lambda_out = b lambda_out
   double* nu;        // padded, interior written (ghosts stay zero)
   double* lam;       // padded output: pointwise part written to the interior
   double* faceG;     // per axis: [face][4][NV]
@@ -353,7 +356,7 @@ __global__ void __launch_bounds__(128) adj_cell_kernel(AdjArgs a) {
     double q[NV], dU[NV], mu[NV];
     for (int v = 0; v < NV; ++v) {
       q[v] = a.U[v * g.fstride + o];
-      mu[v] = a.mu[v * g.fstride + o];
+      mu[v] = a.mu_scale * a.lam_out[v * g.fstride + o];
       dU[v] = a.dU[v * g.fstride + o];
     }
     // nu = mu^T dL/d(dU), pointwise mu^T dL/dq, xi partial (f = 1 - 1/xi^2)
@@ -361,7 +364,7 @@ __global__ void __launch_bounds__(128) adj_cell_kernel(AdjArgs a) {
     const double df = rhs_vjp<NV>(q, dU, mu, p, nu, dq);
     for (int v = 0; v < NV; ++v) {
       a.nu[v * g.fstride + o] = nu[v];
-      a.lam[v * g.fstride + o] = dq[v];
+      a.lam[v * g.fstride + o] = fma(a.id_scale, a.lam_out[v * g.fstride + o], dq[v]);
     }
     const double xi = p.xi;
     dxi = df * 2.0 / (xi * xi * xi);
@@ -564,7 +567,6 @@ struct AdjState {
   double* lamA = nullptr;      // padded work arrays
   double* lamB = nullptr;
   double* lamC = nullptr;
-  double* mu = nullptr;
   double* nu = nullptr;
   double* faceG = nullptr;
   double* part = nullptr;
@@ -584,7 +586,6 @@ void rsst_adjoint_free(rsst_handle* h) {
   cudaFree(s->lamA);
   cudaFree(s->lamB);
   cudaFree(s->lamC);
-  cudaFree(s->mu);
   cudaFree(s->nu);
   cudaFree(s->faceG);
   cudaFree(s->part);
@@ -635,7 +636,7 @@ extern "C" int rsst_adjoint_record(rsst_handle* h, double dt, int nsteps, int ev
             cudaMalloc((void**)&s->dUs, 2 * (size_t)every * sb) == cudaSuccess &&
             cudaMalloc((void**)&s->lamA, sb) == cudaSuccess && cudaMalloc((void**)&s->lamB, sb) == cudaSuccess &&
             cudaMalloc((void**)&s->lamC, sb) == cudaSuccess &&
-            cudaMalloc((void**)&s->mu, sb) == cudaSuccess && cudaMalloc((void**)&s->nu, sb) == cudaSuccess &&
+            cudaMalloc((void**)&s->nu, sb) == cudaSuccess &&
             cudaMalloc((void**)&s->faceG, (size_t)faces * 4 * nv * sizeof(double)) == cudaSuccess &&
             cudaMalloc((void**)&s->part, (size_t)s->part_len * sizeof(double)) == cudaSuccess &&
             cudaMalloc((void**)&s->dxi, sizeof(double)) == cudaSuccess;
@@ -675,20 +676,19 @@ extern "C" int rsst_adjoint_segments(rsst_handle* h, int32_t* nseg) {
 // interior, ghosts folded) and adds the xi partials to s->dxi.
 static int stage_vjp(rsst_handle* h, AdjState* s, const double* in, const double* dU, const double* lam_out, double b,
                      double* res) {
+  // No clearing is needed: the cell kernel writes nu and res at every
+  // interior cell, the face kernels read nu at interior cells only, and the
+  // gather writes every edge ghost of res that the fold reads.
   const Geom& g = h->g;
   const int nv = g.ndim + 2;
   cudaStream_t st = h->stream;
-  const size_t sb = state_bytes(h);
-  if (cudaMemsetAsync(s->nu, 0, sb, st) != cudaSuccess || cudaMemsetAsync(res, 0, sb, st) != cudaSuccess) {
-    rsst_set_error("adjoint memset failed");
-    return RSST_ECUDA;
-  }
-  axpby_kernel<<<blocks_for(g.ncells), 128, 0, st>>>(s->mu, lam_out, b * s->dt, nullptr, 0.0, g, nv);
   AdjArgs a;
   memset(&a, 0, sizeof a);
   a.U = in;
   a.dU = dU;
-  a.mu = s->mu;
+  a.lam_out = lam_out;
+  a.mu_scale = b * s->dt;
+  a.id_scale = b;
   a.nu = s->nu;
   a.lam = res;
   a.faceG = s->faceG;
@@ -724,12 +724,8 @@ static int stage_vjp(rsst_handle* h, AdjState* s, const double* in, const double
     case 4: adj_gather_kernel<4><<<blocks_for(padded), 128, 0, st>>>(a); adj_fold_kernel<4><<<cb, 128, 0, st>>>(res, g, h->p); break;
     default: adj_gather_kernel<5><<<blocks_for(padded), 128, 0, st>>>(a); adj_fold_kernel<5><<<cb, 128, 0, st>>>(res, g, h->p); break;
   }
-  rc = launch_err("adjoint gather/fold");
-  if (rc) return rc;
-  // res += b * lam_out (identity part of the stage)
-  axpby_kernel<<<cb, 128, 0, st>>>(res, res, 1.0, lam_out, b, g, nv);
-  h->launches += 6 + g.ndim;
-  return launch_err("adjoint combine");
+  h->launches += 4 + g.ndim;
+  return launch_err("adjoint gather/fold");
 }
 
 extern "C" int rsst_adjoint_step(rsst_handle* h, int32_t seg, double* lam, double* dJ_dxi) {
