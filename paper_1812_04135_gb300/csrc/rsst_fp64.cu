@@ -76,12 +76,16 @@ struct TileCfg {
   static constexpr int FY = NDIM >= 2 ? BX * (BY + 1) * BZ : 0;
   static constexpr int FZ = NDIM >= 3 ? BX * BY * (BZ + 1) : 0;
   static constexpr int FMAX = FX > FY ? (FX > FZ ? FX : FZ) : (FY > FZ ? FY : FZ);
-  // 1D/2D tiles keep each cell's MC slope along the current axis in shared
-  // memory (cells -1 .. B along that axis), computed once per cell instead
-  // of once per face side; 3D tiles recompute them (shared memory is short).
-  static constexpr bool SLOPES = NDIM <= 2;
+  // Tiles keep each cell's MC slope along the current axis in shared memory
+  // (cells -1 .. B along that axis), computed once per cell instead of once
+  // per face side, when the slope array still leaves room for several CTAs
+  // per SM; larger 3D tiles recompute them per face.
   static constexpr int EX0 = (BX + 2) * BY * BZ, EX1 = NDIM >= 2 ? BX * (BY + 2) * BZ : 0;
-  static constexpr int SEMAX = SLOPES ? (EX0 > EX1 ? EX0 : EX1) : 0;
+  static constexpr int EX2 = NDIM >= 3 ? BX * BY * (BZ + 2) : 0;
+  static constexpr int EXM = EX0 > EX1 ? (EX0 > EX2 ? EX0 : EX2) : (EX1 > EX2 ? EX1 : EX2);
+  static constexpr bool SLOPES =
+      NDIM <= 2 || sizeof(double) * (size_t)NV * (SCELLS + FMAX + EXM) <= (size_t)76 * 1024;
+  static constexpr int SEMAX = SLOPES ? EXM : 0;
   static constexpr size_t SMEM = sizeof(double) * (size_t)NV * (SCELLS + FMAX + SEMAX) + 64 * sizeof(double);
 };
 
@@ -431,7 +435,7 @@ int rsst_launch_stage_fp64(const StageArgs<double>& a, cudaStream_t s) {
       if (a.g.n[0] <= RSST_SMALL_1D) return launch_stage<1, 16, 1, 1, 32>(a, s);
       return launch_stage<1, 256, 1, 1, 256>(a, s);
     case 2: return launch_stage<2, 32, 8, 1, 288>(a, s);  // 9 warps: every face and slope pass in one round
-    case 3: return launch_stage<3, 16, 8, 4, 320>(a, s);  // 10 warps: each face pass in two rounds
+    case 3: return launch_stage<3, 8, 8, 4, 320>(a, s);  // slopes in shared memory; 10 warps: each face pass in one round
   }
   rsst_set_error("ndim must be 1, 2 or 3");
   return RSST_EINVAL;
