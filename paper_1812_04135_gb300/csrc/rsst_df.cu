@@ -444,7 +444,7 @@ int rsst_launch_stage_df(const StageArgs<float2>& sa, cudaStream_t s) {
       if (a.g.n[0] <= RSST_SMALL_1D) return launch_df<1, 16, 1, 1, 32>(a, s);
       return launch_df<1, 256, 1, 1, 256>(a, s);
     case 2: return launch_df<2, 32, 8, 1, 288>(a, s);  // 9 warps: each face pass in one round
-    case 3: return launch_df<3, 16, 8, 4, 256>(a, s);
+    case 3: return launch_df<3, 8, 8, 4, 320>(a, s);  // 10 warps: each face pass in one round
   }
   rsst_set_error("ndim must be 1, 2 or 3");
   return RSST_EINVAL;
