@@ -92,19 +92,43 @@ struct TileCfgDF {
   static constexpr int FY = NDIM >= 2 ? BX * (BY + 1) * BZ : 0;
   static constexpr int FZ = NDIM >= 3 ? BX * BY * (BZ + 1) : 0;
   static constexpr int FMAX = FX > FY ? (FX > FZ ? FX : FZ) : (FY > FZ ? FY : FZ);
-  static constexpr size_t SMEM = sizeof(df) * ((size_t)NV * (SCELLS + FMAX) + 64);
+  // each cell's MC slope along the current axis, once per cell (cells -1 .. B
+  // along that axis), when it fits beside the tile with room for several CTAs
+  static constexpr int EX0 = (BX + 2) * BY * BZ, EX1 = NDIM >= 2 ? BX * (BY + 2) * BZ : 0;
+  static constexpr int EX2 = NDIM >= 3 ? BX * BY * (BZ + 2) : 0;
+  static constexpr int EXM = EX0 > EX1 ? (EX0 > EX2 ? EX0 : EX2) : (EX1 > EX2 ? EX1 : EX2);
+  static constexpr bool SLOPES = NDIM <= 2 || sizeof(df) * (size_t)NV * (SCELLS + FMAX + EXM) <= (size_t)76 * 1024;
+  static constexpr int SEMAX = SLOPES ? EXM : 0;
+  static constexpr size_t SMEM = sizeof(df) * ((size_t)NV * (SCELLS + FMAX + SEMAX) + 64);
 };
 
 template <int NDIM, int BX, int BY, int BZ, int NT, int D>
-__device__ __forceinline__ void face_pass_df(const df* __restrict__ su, df* __restrict__ sf, const PhysDF& p,
-                                             const Geom& g, int i0, int j0, int k0,
+__device__ __forceinline__ void face_pass_df(const df* __restrict__ su, df* __restrict__ sf, df* __restrict__ ss,
+                                             const PhysDF& p, const Geom& g, int i0, int j0, int k0,
                                              df (&dU)[TileCfgDF<NDIM, BX, BY, BZ, NT>::CPT][NDIM + 2]) {
   using C = TileCfgDF<NDIM, BX, BY, BZ, NT>;
   constexpr int NV = C::NV;
   constexpr int EX = BX + (D == 0), EY = BY + (D == 1), EZ = BZ + (D == 2);
   constexpr int NF = EX * EY * EZ;
   constexpr int STRIDE = D == 0 ? 1 : (D == 1 ? C::SX : C::SX * C::SY);
+  constexpr int XX = BX + 2 * (D == 0), YY = BY + 2 * (D == 1), ZZ = BZ + 2 * (D == 2);
+  constexpr int NE = XX * YY * ZZ;
   const int baseD = D == 0 ? i0 : (D == 1 ? j0 : k0);
+  if constexpr (C::SLOPES) {
+    for (int e = threadIdx.x; e < NE; e += NT) {
+      const int ex = e % XX;
+      const int t = e / XX;
+      const int ey = t % YY;
+      const int ez = t / YY;
+      const int s0 = (ez - (D == 2) + C::HZ) * C::SX * C::SY + (ey - (D == 1) + C::HY) * C::SX + (ex - (D == 0) + C::HX);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        const df* sv = su + v * C::SCELLS + s0;
+        ss[v * C::SEMAX + e] = mc_df(sv[0] - sv[-STRIDE], sv[STRIDE] - sv[0]);
+      }
+    }
+    __syncthreads();
+  }
   for (int fid = threadIdx.x; fid < NF; fid += NT) {
     const int fx = fid % EX;
     const int t = fid / EX;
@@ -116,13 +140,24 @@ __device__ __forceinline__ void face_pass_df(const df* __restrict__ su, df* __re
     if (!valid) continue;
     const int s0 = (fz + C::HZ) * C::SX * C::SY + (fy + C::HY) * C::SX + (fx + C::HX);
     df qL[NV], qR[NV];
+    if constexpr (C::SLOPES) {
+      constexpr int STRIDE_E = D == 0 ? 1 : (D == 1 ? XX : XX * YY);
+      const int er = ((fz + (D == 2)) * YY + (fy + (D == 1))) * XX + (fx + (D == 0));
 #pragma unroll
-    for (int v = 0; v < NV; ++v) {
-      const df* sv = su + v * C::SCELLS + s0;
-      const df um2 = sv[-2 * STRIDE], um1 = sv[-STRIDE], u0 = sv[0], up1 = sv[STRIDE];
-      const df dm = um1 - um2, d0 = u0 - um1, dp = up1 - u0;
-      qL[v] = um1 + scale(mc_df(dm, d0), 0.5f);
-      qR[v] = u0 - scale(mc_df(d0, dp), 0.5f);
+      for (int v = 0; v < NV; ++v) {
+        const df* sv = su + v * C::SCELLS + s0;
+        qL[v] = sv[-STRIDE] + scale(ss[v * C::SEMAX + er - STRIDE_E], 0.5f);
+        qR[v] = sv[0] - scale(ss[v * C::SEMAX + er], 0.5f);
+      }
+    } else {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        const df* sv = su + v * C::SCELLS + s0;
+        const df um2 = sv[-2 * STRIDE], um1 = sv[-STRIDE], u0 = sv[0], up1 = sv[STRIDE];
+        const df dm = um1 - um2, d0 = u0 - um1, dp = up1 - u0;
+        qL[v] = um1 + scale(mc_df(dm, d0), 0.5f);
+        qR[v] = u0 - scale(mc_df(d0, dp), 0.5f);
+      }
     }
     df F[NV];
     llf_flux_df<NV, D>(qL, qR, p, F);
@@ -169,7 +204,8 @@ __global__ void __launch_bounds__(NT) stage_df_kernel(const DFArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   df* su = reinterpret_cast<df*>(smem_raw);
   df* sf = su + NV * C::SCELLS;
-  df* sred = sf + NV * C::FMAX;
+  df* ss = sf + NV * C::FMAX;  // slopes, when they fit
+  df* sred = ss + NV * C::SEMAX;
   double* sdt = reinterpret_cast<double*>(sred + 32);
   const Geom& g = a.g;
   const PhysDF& p = a.q;
@@ -204,9 +240,9 @@ __global__ void __launch_bounds__(NT) stage_df_kernel(const DFArgs a) {
   for (int c = 0; c < C::CPT; ++c)
 #pragma unroll
     for (int v = 0; v < NV; ++v) dU[c][v] = {0.0f, 0.0f};
-  face_pass_df<NDIM, BX, BY, BZ, NT, 0>(su, sf, p, g, i0, j0, k0, dU);
-  if constexpr (NDIM >= 2) face_pass_df<NDIM, BX, BY, BZ, NT, 1>(su, sf, p, g, i0, j0, k0, dU);
-  if constexpr (NDIM >= 3) face_pass_df<NDIM, BX, BY, BZ, NT, 2>(su, sf, p, g, i0, j0, k0, dU);
+  face_pass_df<NDIM, BX, BY, BZ, NT, 0>(su, sf, ss, p, g, i0, j0, k0, dU);
+  if constexpr (NDIM >= 2) face_pass_df<NDIM, BX, BY, BZ, NT, 1>(su, sf, ss, p, g, i0, j0, k0, dU);
+  if constexpr (NDIM >= 3) face_pass_df<NDIM, BX, BY, BZ, NT, 2>(su, sf, ss, p, g, i0, j0, k0, dU);
 
   df rmax = {0.0f, 0.0f};
   bool ok_all = true;
