@@ -41,6 +41,7 @@ extern "C" const char* rsst_last_error(void) { return g_err; }
 
 
 void rsst_stage2d_box(int* box_x, int* box_y);  // rsst_fp32_2d.cu
+void rsst_stage3d_box(int* box_x, int* box_y);  // rsst_fp32_3d.cu
 
 static int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 
@@ -270,7 +271,9 @@ extern "C" int rsst_init(rsst_handle** out, const rsst_config* cfg, void* stream
   if (cfg->precision == RSST_FP32_PERT && cfg->ndim == 3 && (cfg->vertical == -1 || cfg->vertical == 2)) {
     h->use_tma3d = 1;
     for (int b = 0; b < 2; ++b) {
-      rc = make_tmap_3d(&h->tmap[b], h->buf[b], h->g, nv, 40, 12);
+      int bx, by;
+      rsst_stage3d_box(&bx, &by);
+      rc = make_tmap_3d(&h->tmap[b], h->buf[b], h->g, nv, bx, by);
       if (rc != RSST_OK) goto fail;
     }
   }

@@ -1,6 +1,7 @@
 // Float32 perturbation stage kernel for 3D grids: TMA-streamed z-march.
 //
-// A CTA owns a 32 x 8 block of (x, y) columns and a chunk of CZ z-planes.
+// A CTA owns a 16 x 8 block of (x, y) columns and a chunk of CZ = 16
+// z-planes (the best of a nine-shape sweep on GB300: five CTAs per SM).
 // Planes (with two-cell x/y halos, all five fields; x origin rounded down to
 // a 16-byte boundary) stream through a six-slot shared-memory ring, one
 // cp.async.bulk.tensor per plane issued three planes ahead, each slot with
@@ -18,7 +19,7 @@
 namespace rsst {
 
 struct T3 {
-  static constexpr int NV = 5, BX = 32, BY = 8, NT = BX * BY, CZ = 32, NS = 6;
+  static constexpr int NV = 5, BX = 16, BY = 8, NT = BX * BY, CZ = 16, NS = 6;
   static constexpr int SXP = BX + 8, SYP = BY + 4, XO = 4, YO = 2;
   static constexpr int PLANE = NV * SYP * SXP;  // floats per plane slot
   static constexpr int FXW = BX + 1, FYH = BY + 1;
@@ -300,6 +301,12 @@ __global__ void __launch_bounds__(T3::NT, 2) stage3d_tma_kernel(const __grid_con
 }  // namespace rsst
 
 using namespace rsst;
+
+// TMA box of one plane of the 3D tile (halo included), for the tensor maps.
+void rsst_stage3d_box(int* box_x, int* box_y) {
+  *box_x = T3::SXP;
+  *box_y = T3::SYP;
+}
 
 int rsst_launch_stage3d_tma(const CUtensorMap* tin, const StageArgs<float>& a, cudaStream_t s) {
   const int vert = a.tab ? a.p.vertical : -1;
