@@ -1,8 +1,8 @@
 // Float32 perturbation stage kernel for 2D grids, TMA-staged.
 //
-// One tile = 64 x 24 cells, 192 threads (three CTAs per SM).
+// One tile = 128 x 8 cells, 128 threads (five CTAs per SM).
 //   1. One thread issues a single cp.async.bulk.tensor load of the tile with
-//      its halo for all four fields (box 72 x 28 x 4 of the padded state, the
+//      its halo for all four fields (box 136 x 12 x 4 of the padded state, the
 //      x origin rounded down to a 16-byte boundary, out-of-range parts zero
 //      filled); the others stage the background table rows of the tile.
 //   2. x faces, one per thread in turn (lanes along x, conflict-free), LLF
@@ -20,7 +20,7 @@
 namespace rsst {
 
 template <int VERT>
-__global__ void __launch_bounds__(T2::NT, 3) stage2d_tma_kernel(const __grid_constant__ CUtensorMap tin,
+__global__ void __launch_bounds__(T2::NT, 5) stage2d_tma_kernel(const __grid_constant__ CUtensorMap tin,
                                                                  const StageArgs<float> a) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   TileRun r;

@@ -29,7 +29,7 @@ struct T2Cfg {
   static_assert(SXP <= 256 && SYP <= 256, "TMA box dimensions are at most 256");
 };
 
-using T2 = T2Cfg<64, 24, 8>;  // single-run default (best of a tile sweep on GB300: 3 CTAs of 6 warps per SM)
+using T2 = T2Cfg<128, 8, 8>;  // single-run default (best of a 13-shape sweep on GB300: 5 CTAs of 4 warps per SM)
 
 template <class C>
 __device__ __forceinline__ uint64_t* t2_barrier(unsigned char* smem) {
