@@ -213,8 +213,8 @@ int rsst_batch_step_looped(rsst_batch* b, int nsteps);
 int rsst_batch_dt(rsst_batch* b, double* dts);
 int rsst_batch_sync(rsst_batch* b);
 
-/* Time `steps` batch steps for each of five tile shapes (64x32, 32x32, 64x16,
- * 128x16, 64x24 cells; index 0..4) on the current states (saved and restored around the
+/* Time `steps` batch steps for each of six tile shapes (64x32, 32x32, 64x16,
+ * 128x16, 64x24, 128x8 cells; index 0..5) on the current states (saved and restored around the
  * trials), keep the fastest; *choice_out gets its index and *ms_out the
  * milliseconds per step (either may be NULL).  With RSST_TUNE_CACHE set to a
  * file name the choice is read from / appended to that file, keyed by the

@@ -93,9 +93,10 @@ using TC1 = T2Cfg<32, 32, 8>;
 using TC2 = T2Cfg<64, 16, 4>;
 using TC3 = T2Cfg<128, 16, 8>;
 using TC4 = T2Cfg<64, 24, 8>;
-constexpr int NCAND = 5;
-static const int CAND_BX[NCAND] = {64, 32, 64, 128, 64};
-static const int CAND_BY[NCAND] = {32, 32, 16, 16, 24};
+using TC5 = T2Cfg<128, 8, 8>;
+constexpr int NCAND = 6;
+static const int CAND_BX[NCAND] = {64, 32, 64, 128, 64, 128};
+static const int CAND_BY[NCAND] = {32, 32, 16, 16, 24, 8};
 
 }  // namespace rsst
 
@@ -139,7 +140,8 @@ static void* cand_kernel(int c, int* nt, size_t* smem) {
     case 1: *nt = TC1::NT; *smem = TC1::smem_bytes(); return kernel_of<TC1>();
     case 2: *nt = TC2::NT; *smem = TC2::smem_bytes(); return kernel_of<TC2>();
     case 3: *nt = TC3::NT; *smem = TC3::smem_bytes(); return kernel_of<TC3>();
-    default: *nt = TC4::NT; *smem = TC4::smem_bytes(); return kernel_of<TC4>();
+    case 4: *nt = TC4::NT; *smem = TC4::smem_bytes(); return kernel_of<TC4>();
+    default: *nt = TC5::NT; *smem = TC5::smem_bytes(); return kernel_of<TC5>();
   }
 }
 
@@ -219,7 +221,8 @@ static int launch_stage(rsst_batch* b, int stage, int slot) {
     case 1: batch_stage_kernel<TC1><<<b->grid, nt, smem, b->stream>>>(b->d_runs, b->d_tile_begin, b->nruns, b->total_tiles, stage, slot); break;
     case 2: batch_stage_kernel<TC2><<<b->grid, nt, smem, b->stream>>>(b->d_runs, b->d_tile_begin, b->nruns, b->total_tiles, stage, slot); break;
     case 3: batch_stage_kernel<TC3><<<b->grid, nt, smem, b->stream>>>(b->d_runs, b->d_tile_begin, b->nruns, b->total_tiles, stage, slot); break;
-    default: batch_stage_kernel<TC4><<<b->grid, nt, smem, b->stream>>>(b->d_runs, b->d_tile_begin, b->nruns, b->total_tiles, stage, slot); break;
+    case 4: batch_stage_kernel<TC4><<<b->grid, nt, smem, b->stream>>>(b->d_runs, b->d_tile_begin, b->nruns, b->total_tiles, stage, slot); break;
+    default: batch_stage_kernel<TC5><<<b->grid, nt, smem, b->stream>>>(b->d_runs, b->d_tile_begin, b->nruns, b->total_tiles, stage, slot); break;
   }
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {

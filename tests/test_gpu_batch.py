@@ -67,8 +67,8 @@ def test_autotune_keeps_the_state_and_picks_a_shape():
         b.set_state(i, torch.from_numpy(w["U"]).cuda())
     before = [b.get_state(i, "cpu") for i in range(len(ws))]
     choice, ms = b.autotune(2)
-    assert 0 <= choice < 5 and ms > 0
-    assert b.tile_shape() in [(64, 32), (32, 32), (64, 16), (128, 16), (64, 24)]
+    assert 0 <= choice < 6 and ms > 0
+    assert b.tile_shape() in [(64, 32), (32, 32), (64, 16), (128, 16), (64, 24), (128, 8)]
     for i in range(len(ws)):
         assert torch.equal(b.get_state(i, "cpu"), before[i])
     b.step(3)
@@ -76,7 +76,7 @@ def test_autotune_keeps_the_state_and_picks_a_shape():
     b.close()
 
 
-@pytest.mark.parametrize("choice_shape", [0, 1, 2, 3, 4])
+@pytest.mark.parametrize("choice_shape", [0, 1, 2, 3, 4, 5])
 def test_every_tile_shape_is_correct(choice_shape, monkeypatch, tmp_path):
     """Force each candidate through the tuning cache and check the result."""
     ws = small_batch(4)
