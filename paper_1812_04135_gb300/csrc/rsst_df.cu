@@ -4,6 +4,7 @@
 // float32 pipe.  Tile structure as in the float64 kernel (rsst_fp64.cu).
 #include "rsst_common.cuh"
 #include "rsst_internal.h"
+#include "rsst_attr.h"
 #include "rsst_math_df.cuh"
 
 namespace rsst {
@@ -438,13 +439,10 @@ static int launch_df(const DFArgs& a, cudaStream_t s) {
   using C = TileCfgDF<NDIM, BX, BY, BZ, NT>;
   auto kern = stage_df_kernel<NDIM, BX, BY, BZ, NT>;
   const size_t smem = C::SMEM + 64;
-  static bool attr = false;
-  if (!attr) {
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
-      rsst_set_error("cudaFuncSetAttribute failed for the double-float stage kernel");
-      return RSST_ECUDA;
-    }
-    attr = true;
+  static std::atomic<unsigned long long> attr{0};
+  if (set_smem_limit_once(kern, smem, attr) != cudaSuccess) {
+    rsst_set_error("cudaFuncSetAttribute failed for the double-float stage kernel");
+    return RSST_ECUDA;
   }
   dim3 grid((a.g.n[0] + BX - 1) / BX, NDIM >= 2 ? (a.g.n[1] + BY - 1) / BY : 1, NDIM >= 3 ? (a.g.n[2] + BZ - 1) / BZ : 1);
   kern<<<grid, NT, smem, s>>>(a);

@@ -10,6 +10,7 @@
 // rsst_math_fp32.cuh).  Tile structure is that of the float64 kernel.
 #include "rsst_common.cuh"
 #include "rsst_internal.h"
+#include "rsst_attr.h"
 #include "rsst_math_fp32.cuh"
 #include "rsst_math_fp64.cuh"
 
@@ -575,13 +576,10 @@ template <int NDIM, int VERT, int BX, int BY, int BZ, int NT>
 static int launch_stage32(const StageArgs<float>& a, cudaStream_t s) {
   using C = TileCfgF<NDIM, VERT, BX, BY, BZ, NT>;
   auto kern = stage_fp32_kernel<NDIM, VERT, BX, BY, BZ, NT>;
-  static bool attr = false;
-  if (!attr) {
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM) != cudaSuccess) {
-      rsst_set_error("cudaFuncSetAttribute failed for the float32 stage kernel");
-      return RSST_ECUDA;
-    }
-    attr = true;
+  static std::atomic<unsigned long long> attr{0};
+  if (set_smem_limit_once(kern, C::SMEM, attr) != cudaSuccess) {
+    rsst_set_error("cudaFuncSetAttribute failed for the float32 stage kernel");
+    return RSST_ECUDA;
   }
   dim3 grid((a.g.n[0] + BX - 1) / BX, NDIM >= 2 ? (a.g.n[1] + BY - 1) / BY : 1, NDIM >= 3 ? (a.g.n[2] + BZ - 1) / BZ : 1);
   kern<<<grid, NT, C::SMEM, s>>>(a);

@@ -16,6 +16,7 @@
 // persistent kernel (rsst_batch.cu).
 #include "rsst_common.cuh"
 #include "rsst_fp32_2d.cuh"
+#include "rsst_attr.h"
 
 namespace rsst {
 
@@ -75,17 +76,17 @@ int rsst_launch_stage2d_tma(const CUtensorMap* tin, const StageArgs<float>& a, c
   dim3 grid((a.g.n[0] + T2::BX - 1) / T2::BX, (a.g.n[1] + T2::BY - 1) / T2::BY, 1);
   const size_t smem = T2::smem_bytes();
   if (vert == 1) {
-    static bool attr = false;
-    if (!attr) {
-      cudaFuncSetAttribute(stage2d_tma_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      attr = true;
+    static std::atomic<unsigned long long> attr{0};
+    if (set_smem_limit_once(stage2d_tma_kernel<1>, smem, attr) != cudaSuccess) {
+      rsst_set_error("cudaFuncSetAttribute failed for the 2D float32 TMA stage kernel");
+      return RSST_ECUDA;
     }
     stage2d_tma_kernel<1><<<grid, T2::NT, smem, s>>>(*tin, a);
   } else if (vert < 0) {
-    static bool attr = false;
-    if (!attr) {
-      cudaFuncSetAttribute(stage2d_tma_kernel<-1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      attr = true;
+    static std::atomic<unsigned long long> attr{0};
+    if (set_smem_limit_once(stage2d_tma_kernel<-1>, smem, attr) != cudaSuccess) {
+      rsst_set_error("cudaFuncSetAttribute failed for the 2D float32 TMA stage kernel");
+      return RSST_ECUDA;
     }
     stage2d_tma_kernel<-1><<<grid, T2::NT, smem, s>>>(*tin, a);
   } else {

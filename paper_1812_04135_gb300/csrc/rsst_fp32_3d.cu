@@ -15,6 +15,7 @@
 #include "rsst_internal.h"
 #include "rsst_math_fp32.cuh"
 #include "rsst_tma.cuh"
+#include "rsst_attr.h"
 
 namespace rsst {
 
@@ -312,17 +313,17 @@ int rsst_launch_stage3d_tma(const CUtensorMap* tin, const StageArgs<float>& a, c
   const int vert = a.tab ? a.p.vertical : -1;
   dim3 grid((a.g.n[0] + T3::BX - 1) / T3::BX, (a.g.n[1] + T3::BY - 1) / T3::BY, (a.g.n[2] + T3::CZ - 1) / T3::CZ);
   if (vert == 2) {
-    static bool attr = false;
-    if (!attr) {
-      cudaFuncSetAttribute(stage3d_tma_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T3::SMEM);
-      attr = true;
+    static std::atomic<unsigned long long> attr{0};
+    if (set_smem_limit_once(stage3d_tma_kernel<2>, T3::SMEM, attr) != cudaSuccess) {
+      rsst_set_error("cudaFuncSetAttribute failed for the 3D float32 TMA stage kernel");
+      return RSST_ECUDA;
     }
     stage3d_tma_kernel<2><<<grid, T3::NT, T3::SMEM, s>>>(*tin, a);
   } else if (vert < 0) {
-    static bool attr = false;
-    if (!attr) {
-      cudaFuncSetAttribute(stage3d_tma_kernel<-1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T3::SMEM);
-      attr = true;
+    static std::atomic<unsigned long long> attr{0};
+    if (set_smem_limit_once(stage3d_tma_kernel<-1>, T3::SMEM, attr) != cudaSuccess) {
+      rsst_set_error("cudaFuncSetAttribute failed for the 3D float32 TMA stage kernel");
+      return RSST_ECUDA;
     }
     stage3d_tma_kernel<-1><<<grid, T3::NT, T3::SMEM, s>>>(*tin, a);
   } else {

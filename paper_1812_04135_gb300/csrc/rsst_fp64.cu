@@ -17,6 +17,7 @@
 
 #include "rsst_common.cuh"
 #include "rsst_internal.h"
+#include "rsst_attr.h"
 #include "rsst_math_fp64.cuh"
 
 namespace rsst {
@@ -407,13 +408,10 @@ template <int NDIM, int BX, int BY, int BZ, int NT>
 static int launch_stage(const StageArgs<double>& a, cudaStream_t s) {
   using C = TileCfg<NDIM, BX, BY, BZ, NT>;
   auto kern = stage_fp64_kernel<NDIM, BX, BY, BZ, NT>;
-  static bool attr = false;
-  if (!attr) {
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM) != cudaSuccess) {
-      rsst_set_error("cudaFuncSetAttribute failed for the float64 stage kernel");
-      return RSST_ECUDA;
-    }
-    attr = true;
+  static std::atomic<unsigned long long> attr{0};
+  if (set_smem_limit_once(kern, C::SMEM, attr) != cudaSuccess) {
+    rsst_set_error("cudaFuncSetAttribute failed for the float64 stage kernel");
+    return RSST_ECUDA;
   }
   dim3 grid((a.g.n[0] + BX - 1) / BX, NDIM >= 2 ? (a.g.n[1] + BY - 1) / BY : 1, NDIM >= 3 ? (a.g.n[2] + BZ - 1) / BZ : 1);
   kern<<<grid, NT, C::SMEM, s>>>(a);
