@@ -161,8 +161,11 @@ int rsst_conserved_sums(rsst_handle* h, double* sums);
  * conserved state and to xi. */
 
 /* Run nsteps fixed-dt steps from the current state, storing a checkpoint of
- * the state every `every` steps (library-owned device memory).  The handle
- * ends at U^{nsteps}.  RSST_EUNSUPPORTED for float32 runs.  Asynchronous. */
+ * the state every `every` steps.  All device memory the adjoint needs is
+ * allocated here (library-owned): ceil(nsteps/every) checkpoints, 2 x every
+ * recompute states and their Euler tendencies, and a few state-sized work
+ * arrays; RSST_ENOMEM if that fails.  The handle ends at U^{nsteps}.
+ * RSST_EUNSUPPORTED for runs that are not float64.  Asynchronous. */
 int rsst_adjoint_record(rsst_handle* h, double dt, int nsteps, int every);
 
 /* Number of recorded segments, ceil(nsteps / every). */
@@ -173,7 +176,7 @@ int rsst_adjoint_segments(rsst_handle* h, int32_t* nseg);
  * device pointer, caller layout, float64; on entry dJ/dU at the segment's end,
  * on return dJ/dU at its start.  *dJ_dxi (host) is incremented by the
  * segment's contribution.  The handle's current state is preserved.
- * Synchronous. */
+ * Allocates nothing.  Synchronous. */
 int rsst_adjoint_step(rsst_handle* h, int32_t seg, double* lam, double* dJ_dxi);
 
 /* J = sum_cells |m|^2/(2 rho) * cell volume of the current state (host

@@ -564,6 +564,7 @@ struct AdjState {
   std::vector<double*> ckpt;   // padded states at steps 0, every, 2 every, ...
   double* stages = nullptr;    // recompute storage: 2 * every padded states
   double* dUs = nullptr;       // their Euler tendencies (same layout)
+  double* save = nullptr;      // the live state while a segment is recomputed
   double* lamA = nullptr;      // padded work arrays
   double* lamB = nullptr;
   double* lamC = nullptr;
@@ -583,6 +584,7 @@ void rsst_adjoint_free(rsst_handle* h) {
   for (double* c : s->ckpt) cudaFree(c);
   cudaFree(s->stages);
   cudaFree(s->dUs);
+  cudaFree(s->save);
   cudaFree(s->lamA);
   cudaFree(s->lamB);
   cudaFree(s->lamC);
@@ -634,6 +636,7 @@ extern "C" int rsst_adjoint_record(rsst_handle* h, double dt, int nsteps, int ev
   const int nv = g.ndim + 2;
   bool ok = cudaMalloc((void**)&s->stages, 2 * (size_t)every * sb) == cudaSuccess &&
             cudaMalloc((void**)&s->dUs, 2 * (size_t)every * sb) == cudaSuccess &&
+            cudaMalloc((void**)&s->save, sb) == cudaSuccess &&
             cudaMalloc((void**)&s->lamA, sb) == cudaSuccess && cudaMalloc((void**)&s->lamB, sb) == cudaSuccess &&
             cudaMalloc((void**)&s->lamC, sb) == cudaSuccess &&
             cudaMalloc((void**)&s->nu, sb) == cudaSuccess &&
@@ -741,38 +744,42 @@ extern "C" int rsst_adjoint_step(rsst_handle* h, int32_t seg, double* lam, doubl
   const int s0 = seg * s->every;
   const int k = (s0 + s->every <= s->nsteps) ? s->every : s->nsteps - s0;
   const int64_t fe = g.fstride * (int64_t)nv;
-  // recompute the segment: stages[2i] = U^{s0+i}, stages[2i+1] = U*
-  double* save_state = nullptr;
-  if (cudaMalloc((void**)&save_state, sb) != cudaSuccess) {
-    cudaGetLastError();
-    rsst_set_error("rsst_adjoint_step: allocation failed");
-    return RSST_ENOMEM;
-  }
+  // recompute the segment: stages[2i] = U^{s0+i}, stages[2i+1] = U*; the
+  // live state and scalars are saved and put back afterwards
+  cudaError_t ce = cudaSuccess;
+  auto chk = [&](cudaError_t e) { if (ce == cudaSuccess && e != cudaSuccess) ce = e; };
   int rc = RSST_OK;
   const int slot0 = h->slot;
   double save_scal[16];
-  cudaMemcpyAsync(h->h_small, h->d_scal, 16 * sizeof(double), cudaMemcpyDeviceToHost, st);
-  cudaStreamSynchronize(st);
+  chk(cudaMemcpyAsync(h->h_small, h->d_scal, 16 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  chk(cudaStreamSynchronize(st));
   memcpy(save_scal, h->h_small, sizeof save_scal);
-  cudaMemcpyAsync(save_state, h->buf[0], sb, cudaMemcpyDeviceToDevice, st);
-  cudaMemcpyAsync(h->buf[0], s->ckpt[seg], sb, cudaMemcpyDeviceToDevice, st);
-  for (int i = 0; i < k && rc == RSST_OK; ++i) {
-    cudaMemcpyAsync(s->stages + (2 * i) * fe, h->buf[0], sb, cudaMemcpyDeviceToDevice, st);
+  chk(cudaMemcpyAsync(s->save, h->buf[0], sb, cudaMemcpyDeviceToDevice, st));
+  chk(cudaMemcpyAsync(h->buf[0], s->ckpt[seg], sb, cudaMemcpyDeviceToDevice, st));
+  for (int i = 0; i < k && rc == RSST_OK && ce == cudaSuccess; ++i) {
+    chk(cudaMemcpyAsync(s->stages + (2 * i) * fe, h->buf[0], sb, cudaMemcpyDeviceToDevice, st));
     h->rec_dU[0] = s->dUs + (2 * i) * fe;      // the forward kernels also write each stage's Euler tendency
     h->rec_dU[1] = s->dUs + (2 * i + 1) * fe;
     rc = rsst_handle_steps(h, s->dt, 1);
     h->rec_dU[0] = h->rec_dU[1] = nullptr;
     // buf[1] still holds U* of this step
-    cudaMemcpyAsync(s->stages + (2 * i + 1) * fe, h->buf[1], sb, cudaMemcpyDeviceToDevice, st);
+    chk(cudaMemcpyAsync(s->stages + (2 * i + 1) * fe, h->buf[1], sb, cudaMemcpyDeviceToDevice, st));
   }
-  cudaMemcpyAsync(h->buf[0], save_state, sb, cudaMemcpyDeviceToDevice, st);
+  chk(cudaMemcpyAsync(h->buf[0], s->save, sb, cudaMemcpyDeviceToDevice, st));
   memcpy(h->h_small, save_scal, sizeof save_scal);
-  cudaMemcpyAsync(h->d_scal, h->h_small, 16 * sizeof(double), cudaMemcpyHostToDevice, st);
-  cudaStreamSynchronize(st);
+  chk(cudaMemcpyAsync(h->d_scal, h->h_small, 16 * sizeof(double), cudaMemcpyHostToDevice, st));
+  chk(cudaStreamSynchronize(st));
+  if (rc == RSST_OK && ce != cudaSuccess) {
+    rsst_set_error("rsst_adjoint_step: segment recompute: %s", cudaGetErrorString(ce));
+    rc = RSST_ECUDA;
+  }
   h->slot = slot0;
   if (rc == RSST_OK) {
-    cudaMemsetAsync(s->dxi, 0, sizeof(double), st);
-    cudaMemsetAsync(s->lamA, 0, sb, st);
+    if (cudaMemsetAsync(s->dxi, 0, sizeof(double), st) != cudaSuccess ||
+        cudaMemsetAsync(s->lamA, 0, sb, st) != cudaSuccess) {
+      rsst_set_error("rsst_adjoint_step: clearing the work arrays failed");
+      return RSST_ECUDA;
+    }
     to_padded_kernel<<<blocks_for(g.ncells), 128, 0, st>>>(lam, s->lamA, g, nv);
     for (int i = k - 1; i >= 0 && rc == RSST_OK; --i) {
       const double* Un = s->stages + (2 * i) * fe;
@@ -801,7 +808,6 @@ extern "C" int rsst_adjoint_step(rsst_handle* h, int32_t seg, double* lam, doubl
   } else {
     cudaStreamSynchronize(st);
   }
-  cudaFree(save_state);
   if (rc == RSST_OK) *dJ_dxi += dx;
   return rc;
 }
