@@ -141,6 +141,24 @@ def _stream_ptr(stream) -> Optional[int]:
 
 # --- the C entry points, same names -----------------------------------------
 
+def _f64_ptr(U, where: str, on_host: bool = False) -> int:
+    """Address of a contiguous float64 buffer, checked against where it must
+    live: host memory (numpy array or CPU tensor) when ``on_host``, else a
+    CUDA tensor.  The C ABI takes bare pointers and cannot check this."""
+    if isinstance(U, np.ndarray):
+        if U.dtype != np.float64 or not U.flags["C_CONTIGUOUS"]:
+            raise ValueError(f"{where}: need a C-contiguous float64 array")
+        if not on_host:
+            raise ValueError(f"{where}: a numpy array is host memory; pass on_host=True or a CUDA tensor")
+        return U.ctypes.data
+    import torch
+    if not isinstance(U, torch.Tensor) or U.dtype != torch.float64 or not U.is_contiguous():
+        raise ValueError(f"{where}: need a contiguous float64 tensor")
+    if U.is_cuda == bool(on_host):
+        raise ValueError(f"{where}: tensor on {U.device} but on_host={bool(on_host)}")
+    return U.data_ptr()
+
+
 def rsst_init(cfg: Config, stream=None) -> int:
     h = C.c_void_p()
     _check(lib().rsst_init(C.byref(h), C.byref(cfg), _stream_ptr(stream)), "rsst_init")
@@ -153,12 +171,12 @@ def rsst_destroy(h: int) -> None:
 
 def rsst_set_state(h: int, U, on_host: bool = False) -> None:
     """U: float64 tensor or ndarray in the caller layout [nvar][nz][ny][nx], contiguous."""
-    ptr = U.ctypes.data if isinstance(U, np.ndarray) else U.data_ptr()
+    ptr = _f64_ptr(U, "rsst_set_state", on_host)
     _check(lib().rsst_set_state(h, ptr, int(on_host)), "rsst_set_state")
 
 
 def rsst_get_state(h: int, U, on_host: bool = False) -> None:
-    ptr = U.ctypes.data if isinstance(U, np.ndarray) else U.data_ptr()
+    ptr = _f64_ptr(U, "rsst_get_state", on_host)
     _check(lib().rsst_get_state(h, ptr, int(on_host)), "rsst_get_state")
 
 
@@ -194,8 +212,9 @@ def rsst_conserved_sums_noalloc(U, n, dx, sums, stream=None) -> None:
     ndim = len(n)
     nn = (C.c_int32 * ndim)(*[int(v) for v in n])
     dd = (C.c_double * ndim)(*[float(v) for v in dx])
-    _check(lib().rsst_conserved_sums_noalloc(U.data_ptr(), ndim, nn, dd, sums.data_ptr(), _stream_ptr(stream)),
-           "rsst_conserved_sums_noalloc")
+    pu = _f64_ptr(U, "rsst_conserved_sums_noalloc")
+    ps = _f64_ptr(sums, "rsst_conserved_sums_noalloc")
+    _check(lib().rsst_conserved_sums_noalloc(pu, ndim, nn, dd, ps, _stream_ptr(stream)), "rsst_conserved_sums_noalloc")
 
 
 def rsst_adjoint_record(h: int, dt: float, nsteps: int, every: int) -> None:
@@ -211,13 +230,15 @@ def rsst_adjoint_segments(h: int) -> int:
 def rsst_adjoint_step(h: int, seg: int, lam) -> float:
     """Reverse one segment in place on ``lam`` (float64 CUDA tensor, caller layout); returns dJ/dxi of it."""
     acc = C.c_double(0.0)
-    _check(lib().rsst_adjoint_step(h, int(seg), lam.data_ptr(), C.byref(acc)), "rsst_adjoint_step")
+    ptr = _f64_ptr(lam, "rsst_adjoint_step")
+    _check(lib().rsst_adjoint_step(h, int(seg), ptr, C.byref(acc)), "rsst_adjoint_step")
     return acc.value
 
 
 def rsst_kinetic_energy(h: int, grad=None) -> float:
     J = C.c_double()
-    _check(lib().rsst_kinetic_energy(h, C.byref(J), None if grad is None else grad.data_ptr()), "rsst_kinetic_energy")
+    ptr = None if grad is None else _f64_ptr(grad, "rsst_kinetic_energy")
+    _check(lib().rsst_kinetic_energy(h, C.byref(J), ptr), "rsst_kinetic_energy")
     return J.value
 
 
@@ -255,7 +276,8 @@ class Solver:
         if isinstance(U, np.ndarray):
             U = torch.from_numpy(np.ascontiguousarray(U, dtype=np.float64))
         U = U.contiguous()
-        assert U.dtype == torch.float64 and tuple(U.shape) == self.shape, (U.dtype, U.shape, self.shape)
+        if U.dtype != torch.float64 or tuple(U.shape) != self.shape:
+            raise ValueError(f"set_state: need float64 of shape {self.shape}, got {U.dtype} {tuple(U.shape)}")
         self._keep = U
         rsst_set_state(self.h, U, on_host=not U.is_cuda)
 
@@ -312,12 +334,12 @@ def rsst_batch_destroy(b: int) -> None:
 
 
 def rsst_batch_set_state(b: int, run: int, U, on_host: bool = False) -> None:
-    ptr = U.ctypes.data if isinstance(U, np.ndarray) else U.data_ptr()
+    ptr = _f64_ptr(U, "rsst_batch_set_state", on_host)
     _check(lib().rsst_batch_set_state(b, run, ptr, int(on_host)), "rsst_batch_set_state")
 
 
 def rsst_batch_get_state(b: int, run: int, U, on_host: bool = False) -> None:
-    ptr = U.ctypes.data if isinstance(U, np.ndarray) else U.data_ptr()
+    ptr = _f64_ptr(U, "rsst_batch_get_state", on_host)
     _check(lib().rsst_batch_get_state(b, run, ptr, int(on_host)), "rsst_batch_get_state")
 
 
@@ -372,6 +394,10 @@ class BatchSolver:
         if isinstance(U, np.ndarray):
             U = torch.from_numpy(np.ascontiguousarray(U, dtype=np.float64))
         U = U.contiguous()
+        w = self.ws[run]
+        shape = (w["ndim"] + 2,) + tuple(reversed(w["n"]))
+        if U.dtype != torch.float64 or tuple(U.shape) != shape:
+            raise ValueError(f"set_state: need float64 of shape {shape}, got {U.dtype} {tuple(U.shape)}")
         self._keep = getattr(self, "_keep", {})
         self._keep[run] = U
         rsst_batch_set_state(self.b, run, U, on_host=not U.is_cuda)
@@ -436,6 +462,7 @@ def _make_rsst_run():
             solver.set_state(U0.detach().to(torch.float64).contiguous())
             rsst_adjoint_record(solver.h, dt, nsteps, every)
             ctx.solver = solver
+            ctx.xi_device = xi.device if isinstance(xi, torch.Tensor) else None
             return solver.get_state(U0.device if U0.is_cuda else "cuda").to(U0.device)
 
         @staticmethod
@@ -445,7 +472,8 @@ def _make_rsst_run():
             dxi = 0.0
             for seg in reversed(range(rsst_adjoint_segments(s.h))):
                 dxi += rsst_adjoint_step(s.h, seg, lam)
-            return lam.to(gN.device), torch.tensor(dxi, dtype=torch.float64, device=gN.device), None, None, None, None
+            gxi = torch.tensor(dxi, dtype=torch.float64, device=ctx.xi_device) if ctx.xi_device is not None else None
+            return lam.to(gN.device), gxi, None, None, None, None
 
     return RsstRun
 

@@ -63,3 +63,20 @@ def test_invalid_config_rejected_without_gpu(L, bad):
 def test_graph_steps_rejects_null_handle_and_odd_k(L):
     assert L.rsst_set_graph_steps(None, 16) == rsst.RSST_EINVAL
     assert L.rsst_set_graph_steps(None, 3) == rsst.RSST_EINVAL
+
+
+def test_binding_rejects_wrong_buffers_before_the_library():
+    """The C ABI takes bare pointers; the binding checks dtype, contiguity and
+    where the buffer lives before any call reaches the library."""
+    import numpy as np
+    import torch
+    with pytest.raises(ValueError):
+        rsst.rsst_set_state(0, np.zeros(8, dtype=np.float32), on_host=True)
+    with pytest.raises(ValueError):
+        rsst.rsst_set_state(0, np.zeros(8), on_host=False)          # host array passed as device memory
+    with pytest.raises(ValueError):
+        rsst.rsst_get_state(0, torch.zeros(8, dtype=torch.float64), on_host=False)
+    with pytest.raises(ValueError):
+        rsst.rsst_set_state(0, torch.zeros(4, 4, dtype=torch.float64).t(), on_host=True)  # not contiguous
+    with pytest.raises(ValueError):
+        rsst.rsst_adjoint_step(0, 0, torch.zeros(8, dtype=torch.float64))                 # must be a CUDA tensor
