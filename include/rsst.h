@@ -18,6 +18,11 @@
  *  - State layout seen by the caller (device or host memory, float64):
  *    structure of arrays [nvar][nz][ny][nx], x fastest, nvar = 2 + ndim,
  *    components (rho, m_x[, m_y[, m_z]], E).  Unused dimensions have size 1.
+ *  - Buffers documented as device memory must be cudaMalloc'd or managed
+ *    memory, host buffers (on_host = 1) pageable or pinned host memory; the
+ *    kind is checked (cudaPointerGetAttributes) and a wrong one returns
+ *    RSST_EINVAL before anything runs.  Sizes cannot be checked: a buffer
+ *    must hold the layout stated for the call.
  *  - The caller owns every buffer it passes.  The library owns its working
  *    state (padded, with two ghost layers per active axis), its CFL scalars,
  *    flags, graphs and checkpoints; rsst_destroy frees them.

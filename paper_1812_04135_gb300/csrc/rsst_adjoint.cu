@@ -31,6 +31,7 @@
 
 #include "rsst_common.cuh"
 #include "rsst_internal.h"
+#include "rsst_check.h"
 #include "rsst_math_fp64.cuh"
 
 namespace rsst {
@@ -737,6 +738,7 @@ extern "C" int rsst_adjoint_step(rsst_handle* h, int32_t seg, double* lam, doubl
     rsst_set_error("rsst_adjoint_step: bad arguments or no recorded run");
     return RSST_EINVAL;
   }
+  if (rsst_check_buffer(lam, 0, "rsst_adjoint_step (lam)") != RSST_OK) return RSST_EINVAL;
   const Geom& g = h->g;
   const int nv = g.ndim + 2;
   const size_t sb = state_bytes(h);
@@ -814,6 +816,7 @@ extern "C" int rsst_adjoint_step(rsst_handle* h, int32_t seg, double* lam, doubl
 
 extern "C" int rsst_kinetic_energy(rsst_handle* h, double* J, double* grad) {
   if (!h || !J) { rsst_set_error("rsst_kinetic_energy: NULL argument"); return RSST_EINVAL; }
+  if (grad && rsst_check_buffer(grad, 0, "rsst_kinetic_energy (grad)") != RSST_OK) return RSST_EINVAL;
   if (h->cfg.precision != RSST_FP64) { rsst_set_error("rsst_kinetic_energy: float64 runs only"); return RSST_EUNSUPPORTED; }
   const Geom& g = h->g;
   const int nb = blocks_for(g.ncells);

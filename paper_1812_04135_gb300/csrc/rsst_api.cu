@@ -11,6 +11,7 @@
 #include <type_traits>
 
 #include "rsst_internal.h"
+#include "rsst_check.h"
 
 static thread_local char g_err[512] = "";
 
@@ -22,6 +23,29 @@ void rsst_set_error(const char* fmt, ...) {
 }
 
 extern "C" const char* rsst_last_error(void) { return g_err; }
+
+int rsst_check_buffer(const void* p, int on_host, const char* where) {
+  if (!p) {
+    rsst_set_error("%s: NULL buffer", where);
+    return RSST_EINVAL;
+  }
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    rsst_set_error("%s: cannot query the buffer's memory type", where);
+    return RSST_EINVAL;
+  }
+  const bool dev = a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+  if (!on_host && !dev) {
+    rsst_set_error("%s: on_host = 0 but the buffer is host memory", where);
+    return RSST_EINVAL;
+  }
+  if (on_host && a.type == cudaMemoryTypeDevice) {
+    rsst_set_error("%s: on_host = 1 but the buffer is device memory", where);
+    return RSST_EINVAL;
+  }
+  return RSST_OK;
+}
 
 #define CUDA_TRY(call)                                                              \
   do {                                                                              \
@@ -298,6 +322,7 @@ static int check_flag(rsst_handle* h) {
 
 extern "C" int rsst_set_state(rsst_handle* h, const double* U, int on_host) {
   if (!h || !U) { rsst_set_error("NULL argument"); return RSST_EINVAL; }
+  RC_TRY(rsst_check_buffer(U, on_host, "rsst_set_state"));
   const int nv = h->g.ndim + 2;
   const size_t bytes = (size_t)nv * h->g.ncells * sizeof(double);
   const double* src = U;
@@ -329,6 +354,7 @@ extern "C" int rsst_set_state(rsst_handle* h, const double* U, int on_host) {
 
 extern "C" int rsst_get_state(rsst_handle* h, double* U, int on_host) {
   if (!h || !U) { rsst_set_error("NULL argument"); return RSST_EINVAL; }
+  RC_TRY(rsst_check_buffer(U, on_host, "rsst_get_state"));
   const int nv = h->g.ndim + 2;
   const size_t bytes = (size_t)nv * h->g.ncells * sizeof(double);
   double* dst = on_host ? h->d_stage : U;

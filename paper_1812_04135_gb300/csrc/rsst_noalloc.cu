@@ -18,6 +18,7 @@
 #include <mutex>
 
 #include "rsst_internal.h"
+#include "rsst_check.h"
 
 #define NOALLOC_BLOCKS 1024
 #define NOALLOC_THREADS 256
@@ -101,6 +102,9 @@ extern "C" int rsst_conserved_sums_noalloc(const double* U, int32_t ndim, const 
     rsst_set_error("rsst_conserved_sums_noalloc: NULL argument");
     return RSST_EINVAL;
   }
+  if (rsst_check_buffer(U, 0, "rsst_conserved_sums_noalloc (U)") != RSST_OK ||
+      rsst_check_buffer(sums, 0, "rsst_conserved_sums_noalloc (sums)") != RSST_OK)
+    return RSST_EINVAL;
   if (ndim < 1 || ndim > 3) {
     rsst_set_error("rsst_conserved_sums_noalloc: ndim must be 1, 2 or 3 (got %d); the scratch holds at most %d fields",
                    ndim, NOALLOC_MAX_FIELDS);

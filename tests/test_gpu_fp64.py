@@ -218,3 +218,22 @@ def test_long_1d_lines_use_wide_tiles(n):
     256-cell tiles: both shapes, and the boundary between them, match."""
     w = inputs.random_smooth_state(1, (n,), xi=6.0, variant="pvs", bc=("reflect",), grav=(0.5, 0.0, 0.0))
     _assert_close(gpu_run(w, 3), oracle_run(w, 3), w["gamma"], what=n)
+
+
+def test_c_abi_rejects_the_wrong_kind_of_buffer():
+    """The C ABI itself (below the binding's checks) refuses a host buffer
+    passed as device memory and a device buffer passed as host memory, with
+    RSST_EINVAL and before any copy or kernel runs.  The host buffer is
+    pinned, so even a missed check could not make the GPU fault."""
+    w = inputs.random_smooth_state(2, (16, 12), xi=3.0)
+    s = rsst.Solver(w, "fp64")
+    L = rsst.lib()
+    host = torch.from_numpy(w["U"]).pin_memory()
+    dev = torch.from_numpy(w["U"]).cuda()
+    assert L.rsst_set_state(s.h, host.data_ptr(), 0) == rsst.RSST_EINVAL
+    assert b"host memory" in L.rsst_last_error()
+    assert L.rsst_get_state(s.h, dev.data_ptr(), 1) == rsst.RSST_EINVAL
+    assert L.rsst_set_state(s.h, dev.data_ptr(), 0) == rsst.RSST_OK
+    assert L.rsst_get_state(s.h, host.data_ptr(), 1) == rsst.RSST_OK
+    assert torch.equal(host, torch.from_numpy(w["U"]))
+    s.close()
