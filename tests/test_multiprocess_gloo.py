@@ -43,3 +43,23 @@ def test_two_gloo_ranks_replicas():
     tmax, value = out[0]
     assert tmax == 2.0
     assert value == pytest.approx(1000 * 2 * 5 * 2 / 2.0)
+
+
+def test_two_rank_launch_prints_one_line_from_rank_zero():
+    """bench.py launched the way multi-GPU runs are launched (torch.distributed.run,
+    two ranks, 127.0.0.1), here on gloo with the CPU oracle arm: rank 0 alone
+    prints the one JSON line and every rank exits 0."""
+    import json
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, RSST_DIST_BACKEND="gloo", OMP_NUM_THREADS="1")
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
+           "--master-addr", "127.0.0.1", "--master-port", str(_free_port()),
+           "bench.py", "--impl", "reference", "--gpus", "2", "--steps", "1", "--warmup", "0"]
+    r = subprocess.run(cmd, cwd=root, env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1, r.stdout
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
