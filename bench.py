@@ -457,8 +457,7 @@ def run_adjoint(args, world, rank, local):
     print(json.dumps(line), flush=True)
 
 
-def cpu_baseline(w, seconds: float):
-    """The oracle as it stands on the host cores: full-grid steps until ~``seconds``."""
+def _oracle_rate(w, seconds: float):
     from oracle import rsst_oracle as ro
     from oracle.workload import problem_from
     prob, U = problem_from(w)
@@ -472,9 +471,24 @@ def cpu_baseline(w, seconds: float):
         el = time.perf_counter() - t0
         if el >= seconds:
             break
-    return {"value": cells * 2 * steps / el, "unit": UNIT, "cores": torch.get_num_threads(), "kind": "oracle",
+    return cells * 2 * steps / el, steps, el
+
+
+def cpu_baseline(w, seconds: float):
+    """The oracle as it stands on the host cores: full-grid steps until
+    ~``seconds``; then a shorter sample on one core."""
+    v, steps, el = _oracle_rate(w, seconds)
+    threads = torch.get_num_threads()
+    torch.set_num_threads(1)
+    try:
+        v1, steps1, el1 = _oracle_rate(w, max(2.0, seconds / 4))
+    finally:
+        torch.set_num_threads(threads)
+    return {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
             "sample": f"{steps} full-grid SSP-RK2 steps of the {w['n'][0]}x{w['n'][1]} workload "
-                      f"({el:.1f} s, torch CPU float64)"}
+                      f"({el:.1f} s, torch CPU float64)",
+            "single_core": {"value": v1, "unit": UNIT, "cores": 1,
+                            "sample": f"{steps1} full-grid steps ({el1:.1f} s, one thread)"}}
 
 
 def run_reference_adjoint(args):
