@@ -237,3 +237,46 @@ def test_c_abi_rejects_the_wrong_kind_of_buffer():
     assert L.rsst_get_state(s.h, host.data_ptr(), 1) == rsst.RSST_OK
     assert torch.equal(host, torch.from_numpy(w["U"]))
     s.close()
+
+
+def test_shear_layer_512_conservation_by_form():
+    """The 512 x 512 shear layer at xi = 30 (density ratio 10, Mach 0.01), by
+    form: PMS holds total momentum to round-off over 5000 steps (bound
+    10 x steps x eps x sum|m|) while its mass source moves the mass; DMS holds
+    mass and momentum to round-off while it stays physical; the
+    density-reduced forms DVS and DMS become non-physical at the ratio-10
+    interface within 5000 steps (the drawback of Sec. 2.2), reported as
+    RSST_ENONPHYSICAL."""
+    eps = 2.2e-16
+    w = inputs.shear_layer_2d(512, 512, xi=30.0, variant="pms")
+    U = torch.from_numpy(w["U"])
+    vol = 1.0 / (512 * 512)
+    absq = [float(U[k].abs().sum()) * vol for k in range(4)]
+    s = rsst.Solver(w, "fp64")
+    s.set_state(U.cuda())
+    s0 = s.sums()
+    s.step(5000)
+    s1 = s.sums()
+    s.close()
+    for k in (1, 2):
+        assert abs(s1[k] - s0[k]) <= 10 * 5000 * eps * absq[k], (k, s0[k], s1[k])
+    assert abs(s1[0] - s0[0]) > 1e-9 * absq[0]                      # PMS carries a mass source
+    w["variant"] = "dms"
+    s = rsst.Solver(w, "fp64")
+    s.set_state(U.cuda())
+    s0 = s.sums()
+    s.step(200)
+    s1 = s.sums()
+    s.close()
+    for k in (0, 1, 2):
+        assert abs(s1[k] - s0[k]) <= 10 * 200 * eps * absq[k], (k, s0[k], s1[k])
+    for var in ("dvs", "dms"):
+        w["variant"] = var
+        s = rsst.Solver(w, "fp64")
+        s.set_state(U.cuda())
+        with pytest.raises(rsst.RsstError) as e:
+            for _ in range(50):
+                s.step(100)
+                s.sync()
+        assert e.value.code == rsst.RSST_ENONPHYSICAL, var
+        s.close()
