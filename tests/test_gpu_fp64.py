@@ -280,3 +280,38 @@ def test_shear_layer_512_conservation_by_form():
                 s.sync()
         assert e.value.code == rsst.RSST_ENONPHYSICAL, var
         s.close()
+
+
+def _gpu_phase_speed(w, nsteps, every, field):
+    """Phase speed of Fourier mode 1 of P or rho from GPU snapshots every
+    ``every`` steps, with the device's simulated time."""
+    s = rsst.Solver(w, "fp64")
+    s.set_state(torch.from_numpy(w["U"]).cuda())
+    ts, ph = [], []
+    for k in range(nsteps // every + 1):
+        if k:
+            s.step(every)
+        U = s.get_state("cpu").numpy()
+        rho, m, E = U[0], U[1], U[2]
+        q = (w["gamma"] - 1.0) * (E - 0.5 * m * m / rho) if field == "P" else rho
+        ts.append(s.time())
+        ph.append(float(np.angle(np.fft.rfft(q - q.mean())[1])))
+    s.close()
+    slope = np.polyfit(np.array(ts), np.unwrap(np.array(ph)), 1)[0]
+    return -slope / (2 * math.pi)
+
+
+@pytest.mark.parametrize("var,xi", [("pvs", 10.0), ("dvs", 10.0), ("pvs", 1.0), ("dvs", 1.0), ("pms", 10.0)])
+def test_sound_wave_speed_2000_steps(var, xi):
+    """1D N = 256 sound eigenmode, 2000 steps on the GPU: it travels at a/xi
+    (a = 1 here) within 1 % (Sec. 3.1)."""
+    w = inputs.sound_wave_1d(256, xi=xi, variant=var)
+    assert _gpu_phase_speed(w, 2000, 50, "P") == pytest.approx(1.0 / xi, rel=0.01)
+
+
+@pytest.mark.parametrize("var,xi", [("pvs", 10.0), ("pms", 10.0), ("dvs", 1.0)])
+def test_entropy_wave_keeps_flow_speed_2000_steps(var, xi):
+    """The density-10 contact keeps the flow speed u = 0.01 within 2 % over
+    2000 steps on the GPU (the entropy wave is not slowed by xi)."""
+    w = inputs.contact_1d(256, xi=xi, variant=var)
+    assert _gpu_phase_speed(w, 2000, 100, "rho") == pytest.approx(0.01, rel=0.02)
