@@ -5,11 +5,14 @@
 // Fused stage kernel, one CTA per tile of BX x BY x BZ cells:
 //   1. the tile plus two halo layers on every active axis (all fields) is
 //      copied from the padded state into shared memory with coalesced loads;
-//   2. per axis D, every face of the tile gets its LLF flux from the four
-//      cells around it (MC slopes of the two neighbours, face states, flux)
-//      in one code path, so a face shared by two tiles gets bit-identical
-//      values in both (discrete conservation);
-//   3. each cell accumulates -(F_{+} - F_{-})/dx_D in registers;
+//   2. per axis D, the MC slope of every cell along D is computed once into
+//      shared memory (1D/2D tiles and small 3D tiles; larger 3D tiles take
+//      the two slopes per face), then every face of the tile gets twice its
+//      LLF flux, F(qL) + F(qR) - alpha (qR - qL), from the face states of
+//      the two cells beside it; a face shared by two tiles is computed the
+//      same way in both, so both get bit-identical values (discrete
+//      conservation);
+//   3. each cell accumulates -(2F_{+} - 2F_{-}) / (2 dx_D) in registers;
 //   4. epilogue per cell: RSST correction, force, RK combine, store, the
 //      edge ghost cells the cell is the image of, and in stage 2 the CFL
 //      maximum for the next step and the physical-state flag.
