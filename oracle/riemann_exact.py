@@ -17,6 +17,8 @@ import math
 
 
 def _f(p, rho, pk, gamma):
+    """Velocity jump across the wave on one side at star pressure p: a shock
+    (Rankine-Hugoniot) for p > pk, an isentropic rarefaction otherwise."""
     a = math.sqrt(gamma * pk / rho)
     if p > pk:
         A = 2.0 / ((gamma + 1.0) * rho)

@@ -136,7 +136,8 @@ def as_eos(g):
 
 def primitives(U: torch.Tensor, gamma):
     """Return rho, list of V_d, |V|^2, P, a^2 of a conservative state
-    (``gamma``: the ideal-gas ratio or an EOS object)."""
+    (``gamma``: the ideal-gas ratio or an EOS object): V = m/rho, P from
+    E - rho|V|^2/2 through the EOS, a^2 = (dP/drho)_S (Sec. 3.2; Sec. 4.2 step 2)."""
     eos = as_eos(gamma)
     nd = U.shape[0] - 2
     rho = U[0]
@@ -148,7 +149,8 @@ def primitives(U: torch.Tensor, gamma):
 
 
 def _speed(v2: torch.Tensor) -> torch.Tensor:
-    """|V| with a zero (sub)gradient at V = 0."""
+    """|V| of c_tot = |V| + a/xi (Sec. 4.2, reading 2), with a zero
+    (sub)gradient at V = 0 (adjoint reading)."""
     pos = v2 > 0
     return torch.sqrt(torch.where(pos, v2, torch.ones_like(v2))) * pos
 
@@ -186,8 +188,9 @@ def physical_flux(U: torch.Tensor, d: int, gamma: float) -> torch.Tensor:
 # ---------------------------------------------------------------------------
 
 def mc_limiter(a: torch.Tensor, b: torch.Tensor) -> torch.Tensor:
-    """Monotonized-central slope: 0 if ab <= 0, else the smallest in magnitude
-    of 2a, 2b, (a+b)/2 (ties resolved in that order)."""
+    """Monotonized-central slope, named in Sec. 4.2 (reading 1): 0 if ab <= 0,
+    else the smallest in magnitude of 2a, 2b, (a+b)/2 (ties resolved in that
+    order)."""
     aa = 2.0 * a.abs()
     bb = 2.0 * b.abs()
     cc = 0.5 * (a + b).abs()
@@ -208,7 +211,8 @@ def llf_flux(UL: torch.Tensor, UR: torch.Tensor, d: int, gamma: float, xi, cmax=
 
 def _background_state(prob: Problem, k_lo: int, count: int) -> Optional[torch.Tensor]:
     """Background U0 = (rho0, 0, P0/(gamma-1)) at padded vertical indices
-    k_lo..k_lo+count-1 (padded index = interior index + 2)."""
+    k_lo..k_lo+count-1 (padded index = interior index + 2); it enters the
+    wall ghosts of reading 7 (hydrostatic walls, App. B setting)."""
     if prob.bg_rho is None:
         return None
     rho0 = prob.bg_rho[k_lo:k_lo + count].to(DT)
@@ -347,7 +351,9 @@ def has_gravity(prob: Problem) -> bool:
 
 
 def rhs(U: torch.Tensor, prob: Problem) -> torch.Tensor:
-    """L(U): Euler tendency, RSST correction, then the external force."""
+    """L(U) of Sec. 4.2 steps 2-7: Euler tendency (Eq. pvs_dt0), the RSST
+    correction of the chosen form (Sec. 3.2, App. A), then the external
+    force (App. B)."""
     out = rsst_correct(U, euler_tendency(U, prob), prob.variant, prob.gamma, prob.xi, prob.cmax)
     if has_gravity(prob):
         out = out + gravity_source(U, prob)
@@ -359,7 +365,8 @@ def rhs(U: torch.Tensor, prob: Problem) -> torch.Tensor:
 # ---------------------------------------------------------------------------
 
 def cfl_dt(U: torch.Tensor, prob: Problem) -> float:
-    """dt = C / max_cells sum_d c_tot / dx_d with C = prob.cfl (0.4 in the paper)."""
+    """dt = C / max_cells sum_d c_tot / dx_d with C = prob.cfl (Courant
+    number 0.4 of Sec. 4.2; the multi-dimensional sum is reading 3)."""
     with torch.no_grad():
         c = c_tot(U, prob.gamma, float(prob.xi), prob.cmax)
         rate = sum(c / prob.dx[d] for d in range(prob.ndim))
@@ -367,14 +374,16 @@ def cfl_dt(U: torch.Tensor, prob: Problem) -> float:
 
 
 def ssp_rk2_step(U: torch.Tensor, dt, prob: Problem) -> torch.Tensor:
-    """Second-order SSP Runge-Kutta (Shu-Osher form)."""
+    """Second-order SSP Runge-Kutta, Shu-Osher form (Sec. 4.2 step 8, which
+    cites Gottlieb et al. without printing it; reading 4)."""
     Us = U + dt * rhs(U, prob)
     return 0.5 * U + 0.5 * (Us + dt * rhs(Us, prob))
 
 
 def run(U: torch.Tensor, prob: Problem, nsteps: int, dt: Optional[float] = None,
         check: bool = True) -> torch.Tensor:
-    """nsteps SSP-RK2 steps; dt from the CFL rule each step when dt is None."""
+    """nsteps SSP-RK2 steps (Sec. 4.2); dt from the CFL rule each step when
+    dt is None."""
     for _ in range(nsteps):
         h = cfl_dt(U, prob) if dt is None else dt
         U = ssp_rk2_step(U, h, prob)
