@@ -29,6 +29,8 @@
  *  - All GPU work is issued on the stream given to rsst_init (a
  *    cudaStream_t, NULL for the legacy default stream).  Calls documented
  *    as asynchronous return once the work is queued.
+ *  - A handle (or batch) is not thread-safe: calls on one handle must not
+ *    overlap; different handles may be used from different threads.
  *  - A non-physical state (rho <= 0, P <= 0 or a non-finite value) found
  *    by a step sets a sticky device flag; the next synchronous call returns
  *    RSST_ENONPHYSICAL.  The output is still written.  No floors are applied.
@@ -62,7 +64,9 @@ typedef enum {
 } rsst_variant;
 
 typedef enum {
-  RSST_FP64 = 0,      /* state stored and computed in float64 */
+  RSST_FP64 = 0,      /* state stored and computed in float64 (the two square
+                       * roots of c_tot, which only set the LLF dissipation
+                       * and dt, to 2^-40 relative) */
   RSST_FP32_PERT = 1, /* float32 perturbation about a float64 background */
   RSST_FP64_DF = 2    /* double-float: state stored and computed as pairs of
                        * float32 (hi + lo, 48-bit significand) on the float32
