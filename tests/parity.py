@@ -67,3 +67,32 @@ def rel_linf_pert(got, ref, w):
         num = float((got[k] - ref[k]).abs().max())
         out.append(num / den if den > 0 else (0.0 if num == 0.0 else float("inf")))
     return out
+
+
+def permute(w, order):
+    """Relabel the axes of a workload: new axis d is old axis order[d]."""
+    nd = w["ndim"]
+    U = w["U"]                                     # [nvar][z][y][x] (reversed axes)
+    # tensor axis of grid axis d is 1 + (nd - 1 - d)
+    perm = [0] + [1 + (nd - 1 - order[nd - 1 - t]) for t in range(nd)]
+    V = np.ascontiguousarray(np.transpose(U, perm))
+    mom = [V[1 + order[d]] for d in range(nd)]     # momentum components follow their axes
+    V = np.ascontiguousarray(np.stack([V[0]] + mom + [V[nd + 1]]))
+    out = dict(w)
+    out["U"] = V
+    out["n"] = tuple(w["n"][order[d]] for d in range(nd))
+    out["dx"] = tuple(w["dx"][order[d]] for d in range(nd))
+    out["bc"] = tuple(w["bc"][order[d]] for d in range(nd))
+    out["grav"] = tuple(w["grav"][order[d]] for d in range(nd)) + (0.0,) * (3 - nd)
+    out["vertical"] = order.index(w["vertical"])
+    return out
+
+
+def column_1d(w2):
+    """The vertical column x = 0 of a 2D stratified workload as a 1D run along x."""
+    U = w2["U"][:, :, 0]                           # [rho, m_x, m_y, E] along y
+    V = np.ascontiguousarray(np.stack([U[0], U[2], U[3]]))
+    out = dict(w2)
+    out.update(ndim=1, U=V, n=(w2["n"][1],), dx=(w2["dx"][1],), bc=(w2["bc"][1],),
+               grav=(w2["grav"][1], 0.0, 0.0), vertical=0)
+    return out

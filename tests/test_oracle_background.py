@@ -59,3 +59,32 @@ def test_rest_state_in_box_stays_at_rest():
     for var in ("pvs", "pms"):
         prob, U = problem_from(w, variant=var)
         assert torch.equal(ro.run(U, prob, 3), U)
+
+
+@pytest.mark.parametrize("order", [[1, 0]])
+def test_axis_relabelling_commutes_with_the_step_2d(order):
+    """Stepping a stratified box with its axes relabelled (gravity, walls and
+    background along x instead of y) equals relabelling the stepped box: the
+    oracle treats every axis alike (catches an axis-index slip)."""
+    from tests.parity import permute
+    w = inputs.polytrope_2d(12, 20, xi=20.0, contrast=20.0, amp=1e-2)
+    wt = permute(w, order)
+    prob, U = problem_from(w)
+    probt, Ut = problem_from(wt)
+    a = ro.run(U, prob, 3).numpy()
+    b = ro.run(Ut, probt, 3).numpy()
+    back = permute(dict(w, U=a), order)["U"]
+    assert np.allclose(b, back, rtol=0, atol=1e-12 * np.abs(back).max())
+
+
+@pytest.mark.parametrize("order", [[2, 0, 1], [0, 2, 1]])
+def test_axis_relabelling_commutes_with_the_step_3d(order):
+    from tests.parity import permute
+    w = inputs.polytrope_3d(8, 6, 20, xi=50.0, contrast=20.0, amp=1e-2)
+    wt = permute(w, order)
+    prob, U = problem_from(w)
+    probt, Ut = problem_from(wt)
+    a = ro.run(U, prob, 2).numpy()
+    b = ro.run(Ut, probt, 2).numpy()
+    back = permute(dict(w, U=a), order)["U"]
+    assert np.allclose(b, back, rtol=0, atol=1e-12 * np.abs(back).max())
