@@ -100,3 +100,22 @@ def test_every_tile_shape_is_correct(choice_shape, monkeypatch, tmp_path):
         ref = ro.run(U, prob, 3)
         assert max(rel_linf(b.get_state(i, "cpu"), ref, w["gamma"])) < 1e-5, (choice_shape, i)
     b.close()
+
+
+def test_batch_cmax_law_matches_oracle():
+    """Runs under the C_max law (Eq. cx: xi from the local sound speed) in
+    the persistent batch kernel, each against the oracle."""
+    ws = small_batch(5)
+    for w in ws:
+        w["cmax"] = 0.3
+        w["xi"] = 1.0
+    b = rsst.BatchSolver(ws)
+    for i, w in enumerate(ws):
+        b.set_state(i, torch.from_numpy(w["U"]).cuda())
+    b.step(4)
+    b.sync()
+    for i, w in enumerate(ws):
+        prob, U = problem_from(w)
+        err = rel_linf(b.get_state(i, "cpu"), ro.run(U, prob, 4), w["gamma"])
+        assert max(err) < 1e-5, (i, w["n"], err)
+    b.close()
