@@ -119,3 +119,21 @@ def test_batch_cmax_law_matches_oracle():
         err = rel_linf(b.get_state(i, "cpu"), ro.run(U, prob, 4), w["gamma"])
         assert max(err) < 1e-5, (i, w["n"], err)
     b.close()
+
+
+def test_mixed_batch_with_and_without_background():
+    """One batch holding runs with a y background and runs without one
+    (plain float32 storage, periodic and walled), each against the oracle."""
+    ws = small_batch(3) + [inputs.random_smooth_state(2, (50, 34), xi=5.0, variant="pms"),
+                           inputs.random_smooth_state(2, (72, 40), xi=2.0, variant="dvs",
+                                                      bc=("reflect", "periodic"), grav=(0.3, 0.0, 0.0))]
+    b = rsst.BatchSolver(ws)
+    for i, w in enumerate(ws):
+        b.set_state(i, torch.from_numpy(w["U"]).cuda())
+    b.step(4)
+    b.sync()
+    for i, w in enumerate(ws):
+        prob, U = problem_from(w)
+        err = rel_linf(b.get_state(i, "cpu"), ro.run(U, prob, 4), w["gamma"])
+        assert max(err) < 1e-5, (i, w["n"], w["vertical"], err)
+    b.close()
