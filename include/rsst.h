@@ -85,7 +85,9 @@ typedef enum { RSST_BC_PERIODIC = 0, RSST_BC_REFLECT = 1 } rsst_bc;
  * and, in RSST_FP32_PERT mode, the float64 state the float32 perturbation is
  * stored about.  With vertical = -1 there is no background (in
  * RSST_FP32_PERT mode the float32 state is then the full state).  On a
- * periodic vertical axis the ghost entries are ignored (taken by wrap). */
+ * periodic vertical axis the ghost entries are ignored (taken by wrap).
+ * rsst_init reads every entry it uses and rejects (RSST_EINVAL) one that is
+ * not finite with rho > 0 and P > 0; it cannot check the arrays' length. */
 typedef struct rsst_config {
   int32_t ndim;        /* 1, 2 or 3 */
   int32_t n[3];        /* interior cells per axis, >= 2 on active axes */

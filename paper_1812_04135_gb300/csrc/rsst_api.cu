@@ -126,11 +126,23 @@ static int validate(const rsst_config* c) {
   if (c->variant < RSST_EULER || c->variant > RSST_PD) { rsst_set_error("variant %d invalid", c->variant); return RSST_EINVAL; }
   if (c->precision != RSST_FP64 && c->precision != RSST_FP32_PERT && c->precision != RSST_FP64_DF) { rsst_set_error("precision %d invalid", c->precision); return RSST_EINVAL; }
   if (!(c->xi >= 1.0) || !std::isfinite(c->xi)) { rsst_set_error("xi must be finite and >= 1 (got %g)", c->xi); return RSST_EINVAL; }
-  if (!(c->gamma > 1.0)) { rsst_set_error("gamma must be > 1"); return RSST_EINVAL; }
-  if (!(c->cfl > 0.0)) { rsst_set_error("cfl must be > 0"); return RSST_EINVAL; }
+  if (!(c->gamma > 1.0) || !std::isfinite(c->gamma)) { rsst_set_error("gamma must be finite and > 1"); return RSST_EINVAL; }
+  if (!(c->cfl > 0.0) || !std::isfinite(c->cfl)) { rsst_set_error("cfl must be finite and > 0"); return RSST_EINVAL; }
+  for (int d = 0; d < c->ndim; ++d)
+    if (!std::isfinite(c->grav[d])) { rsst_set_error("grav[%d] must be finite", d); return RSST_EINVAL; }
   if (!(c->cmax >= 0.0) || !std::isfinite(c->cmax)) { rsst_set_error("cmax must be >= 0 (0: constant xi)"); return RSST_EINVAL; }
   if (c->vertical < -1 || c->vertical >= c->ndim) { rsst_set_error("vertical axis %d invalid", c->vertical); return RSST_EINVAL; }
   if (c->vertical >= 0 && (!c->bg_rho || !c->bg_p)) { rsst_set_error("background profiles required when vertical >= 0"); return RSST_EINVAL; }
+  if (c->vertical >= 0) {
+    // The entries rsst_init reads: all n + 4 on a wall axis, the interior on a periodic one.
+    const int nvert = c->n[c->vertical];
+    const bool wrap = c->bc[c->vertical] == RSST_BC_PERIODIC;
+    for (int k = wrap ? RSST_G : 0; k < (wrap ? nvert + RSST_G : nvert + 2 * RSST_G); ++k)
+      if (!(c->bg_rho[k] > 0.0) || !(c->bg_p[k] > 0.0) || !std::isfinite(c->bg_rho[k]) || !std::isfinite(c->bg_p[k])) {
+        rsst_set_error("background entry %d must be finite with rho > 0 and P > 0", k);
+        return RSST_EINVAL;
+      }
+  }
   int64_t cells = 1;
   for (int d = 0; d < c->ndim; ++d) cells *= c->n[d];
   if (cells > (int64_t)1 << 31) { rsst_set_error("grid too large (%lld cells)", (long long)cells); return RSST_EINVAL; }
@@ -259,6 +271,7 @@ extern "C" int rsst_init(rsst_handle** out, const rsst_config* cfg, void* stream
     const int nvert = h->g.n[cfg->vertical];
     h->bg_len = nvert + 2 * RSST_G;
     double* tmp = (double*)malloc(2 * h->bg_len * sizeof(double));
+    if (!tmp) { rsst_set_error("host allocation of the background failed"); rc = RSST_ENOMEM; goto fail; }
     for (int k = 0; k < h->bg_len; ++k) {
       int src = k;
       if (cfg->bc[cfg->vertical] == RSST_BC_PERIODIC) src = ((k - RSST_G) % nvert + nvert) % nvert + RSST_G;

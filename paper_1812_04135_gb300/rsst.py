@@ -118,6 +118,11 @@ def make_config(ndim, n, dx, *, variant="pvs", precision="fp64", xi=1.0, gamma=5
     if bg_rho is not None:
         r = np.ascontiguousarray(bg_rho, dtype=np.float64)
         p = np.ascontiguousarray(bg_p, dtype=np.float64)
+        if 0 <= cfg.vertical < ndim:
+            need = cfg.n[cfg.vertical] + 4
+            if r.shape != (need,) or p.shape != (need,):
+                raise ValueError(f"background profiles need n[vertical] + 4 = {need} values "
+                                 f"(got {r.shape}, {p.shape})")
         cfg._keep = [r, p]
         cfg.bg_rho = r.ctypes.data_as(C.POINTER(C.c_double))
         cfg.bg_p = p.ctypes.data_as(C.POINTER(C.c_double))

@@ -5,6 +5,7 @@ import glob
 import os
 import re
 
+import numpy as np
 import pytest
 
 from paper_1812_04135_gb300 import rsst
@@ -58,6 +59,51 @@ def test_invalid_config_rejected_without_gpu(L, bad):
     with pytest.raises(rsst.RsstError) as e:
         rsst.rsst_init(cfg, stream=0)
     assert e.value.code == rsst.RSST_EINVAL
+
+
+@pytest.mark.parametrize("bc,k,field,value", [("reflect", 0, "rho", -1.0), ("reflect", 11, "p", 0.0),
+                                               ("periodic", 5, "rho", float("nan")), ("reflect", 3, "p", float("inf"))])
+def test_bad_background_rejected_without_gpu(L, bc, k, field, value):
+    """rsst_init reads every background entry it uses (all n + 4 on a wall
+    axis, the interior on a periodic one) and rejects a non-physical one
+    before any device call."""
+    rho, p = np.linspace(2.0, 1.0, 12), np.linspace(3.0, 1.0, 12)
+    (rho if field == "rho" else p)[k] = value
+    cfg = rsst.make_config(2, [6, 8, 1], [0.1, 0.1, 0.1], xi=3.0, bc=("periodic", bc), vertical=1, bg_rho=rho, bg_p=p)
+    with pytest.raises(rsst.RsstError) as e:
+        rsst.rsst_init(cfg, stream=0)
+    assert e.value.code == rsst.RSST_EINVAL
+    assert "background" in str(e.value)
+
+
+def test_periodic_background_ghost_entries_are_not_read(L):
+    """On a periodic vertical axis the ghost entries are taken by wrap, so a
+    NaN there passes validation (the call then fails only at the device)."""
+    rho, p = np.linspace(2.0, 1.0, 12), np.linspace(3.0, 1.0, 12)
+    rho[0] = rho[-1] = float("nan")
+    cfg = rsst.make_config(2, [6, 8, 1], [0.1, 0.1, 0.1], xi=3.0, bc=("periodic", "periodic"), vertical=1,
+                           bg_rho=rho, bg_p=p)
+    try:
+        h = rsst.rsst_init(cfg, stream=0)
+    except rsst.RsstError as e:
+        assert "background" not in str(e), str(e)
+    else:
+        rsst.rsst_destroy(h)
+
+
+@pytest.mark.parametrize("field,value", [("grav", float("inf")), ("gamma", float("inf")), ("cfl", float("nan"))])
+def test_non_finite_parameters_rejected_without_gpu(L, field, value):
+    kw = dict(variant="pvs", xi=3.0)
+    kw[field] = (0.0, value, 0.0) if field == "grav" else value
+    cfg = rsst.make_config(2, [8, 8, 1], [0.1, 0.1, 0.1], **kw)
+    with pytest.raises(rsst.RsstError) as e:
+        rsst.rsst_init(cfg, stream=0)
+    assert e.value.code == rsst.RSST_EINVAL
+
+
+def test_binding_checks_background_length():
+    with pytest.raises(ValueError):
+        rsst.make_config(2, [6, 8, 1], [0.1] * 3, vertical=1, bg_rho=np.ones(8), bg_p=np.ones(8))
 
 
 def test_graph_steps_rejects_null_handle_and_odd_k(L):
