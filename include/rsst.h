@@ -110,8 +110,14 @@ typedef struct rsst_config {
 
 typedef struct rsst_handle rsst_handle;
 
-/* Create a solver for one run.  Allocates the working state on the current
- * CUDA device.  `stream` is a cudaStream_t (may be NULL).  Synchronous. */
+/* Create a solver for one run (the inputs of the scheme of Sec. 4.2: state,
+ * form, xi, gamma, force, grid and walls).  Allocates the working state on
+ * the current CUDA device; *h is NULL on failure and everything allocated is
+ * freed.  `stream` is a cudaStream_t (may be NULL).  Errors: RSST_EINVAL for
+ * an invalid config, checked before any device call (ndim, n, dx, bc, form,
+ * precision, xi >= 1, gamma > 1, cfl > 0, cmax >= 0, finite gravity, the
+ * background entries); RSST_ENOMEM when an allocation fails; RSST_ECUDA
+ * when a copy, kernel or tensor-map encoding fails.  Synchronous. */
 int rsst_init(rsst_handle** h, const rsst_config* cfg, void* stream);
 
 /* Free everything the handle owns.  Safe on NULL. */
