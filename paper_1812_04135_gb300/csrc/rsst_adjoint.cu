@@ -611,8 +611,8 @@ static int launch_err(const char* what) {
 }
 
 extern "C" int rsst_adjoint_record(rsst_handle* h, double dt, int nsteps, int every) {
-  if (!h || !(dt > 0.0) || nsteps < 1 || every < 1) {
-    rsst_set_error("rsst_adjoint_record: need a handle, dt > 0, nsteps >= 1, every >= 1");
+  if (!h || !(dt > 0.0) || !std::isfinite(dt) || nsteps < 1 || every < 1) {
+    rsst_set_error("rsst_adjoint_record: need a handle, finite dt > 0, nsteps >= 1, every >= 1");
     return RSST_EINVAL;
   }
   if (h->cfg.precision != RSST_FP64) {
