@@ -100,33 +100,123 @@ def fp64_peak_tflops(sm_mhz: float) -> float:
 
 
 class ClockSampler:
-    """nvidia-smi clocks / throttle reasons every 200 ms during the timed region."""
+    """SM clock and clock-event reasons DURING the timed region.
+
+    NVML (the library nvidia-smi reads; queries only, nothing is set) is
+    opened once at start-up, then read when the region opens and when it
+    closes (so a region of a few milliseconds still has its clock on both
+    sides), and every 100 ms in between from a thread.  A query takes under
+    0.1 ms, but a Python thread polling every 5 ms slowed the launching loop
+    tenfold (the two contend for the interpreter lock), which starved the GPU
+    of work and lowered the very clock being read.  Without
+    NVML, nvidia-smi -lms 200 is started and its first line awaited before
+    the region opens."""
+    INTERVAL_S = 0.1
 
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    # clock-event reason bits of the NVML API
+    BITS = {"sw_power_cap": 0x4, "hw_slowdown": 0x8, "sw_thermal_slowdown": 0x20,
+            "hw_thermal_slowdown": 0x40, "hw_power_brake_slowdown": 0x80}
+    NVML_CLOCK_SM = 1
 
     def __init__(self, index: int):
         self.index = index
         self.proc = None
         self.lines = []
+        self.samples = []      # (sm_mhz, reason_bits) from NVML
+        self.max_mhz = None
+        self.nvml = None
+        self.source = None
+
+    # -- NVML ---------------------------------------------------------------
+    _handles = {}  # device index -> (lib, handle, reasons query, ctypes, max MHz), opened once per process
+
+    @classmethod
+    def open_nvml(cls, index: int) -> bool:
+        """Initialise NVML and find the device once (it takes a few hundred
+        milliseconds: done before warm-up, never between warm-up and the
+        timed region, where the idle GPU would lower its clock)."""
+        if index in cls._handles:
+            return cls._handles[index] is not None
+        cls._handles[index] = None
+        import ctypes as C
+        try:
+            lib = C.CDLL("libnvidia-ml.so.1")
+            if lib.nvmlInit_v2() != 0:
+                return False
+            dev = C.c_void_p()
+            ok = False
+            try:
+                pr = torch.cuda.get_device_properties(index)
+                bus = f"{pr.pci_domain_id:08X}:{pr.pci_bus_id:02X}:{pr.pci_device_id:02X}.0"
+                ok = lib.nvmlDeviceGetHandleByPciBusId_v2(bus.encode(), C.byref(dev)) == 0
+            except Exception:
+                ok = False
+            if not ok and lib.nvmlDeviceGetHandleByIndex_v2(C.c_uint(index), C.byref(dev)) != 0:
+                return False
+            reasons = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+                lib.nvmlDeviceGetCurrentClocksThrottleReasons
+            mx = C.c_uint()
+            max_mhz = float(mx.value) if lib.nvmlDeviceGetMaxClockInfo(dev, cls.NVML_CLOCK_SM, C.byref(mx)) == 0 else None
+            cls._handles[index] = (lib, dev, reasons, C, max_mhz)
+            return True
+        except Exception:
+            return False
+
+    def _nvml_open(self):
+        if not self.open_nvml(self.index):
+            return False
+        lib, dev, reasons, C, self.max_mhz = self._handles[self.index]
+        self.nvml = (lib, dev, reasons, C)
+        return True
+
+    def _nvml_sample(self):
+        lib, dev, reasons, C = self.nvml
+        clk, bits = C.c_uint(), C.c_ulonglong()
+        if lib.nvmlDeviceGetClockInfo(dev, self.NVML_CLOCK_SM, C.byref(clk)) == 0 and \
+                reasons(dev, C.byref(bits)) == 0:
+            self.samples.append((float(clk.value), int(bits.value)))
+
+    def _nvml_loop(self):
+        while not self.stop.wait(self.INTERVAL_S):
+            self._nvml_sample()
+
+    # -- nvidia-smi fallback --------------------------------------------------
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+            self.first.set()
 
     def __enter__(self):
+        self.stop = threading.Event()
+        if self._nvml_open():
+            self.source = "nvml: region open and close, every 100 ms between"
+            self._nvml_sample()
+            self.t = threading.Thread(target=self._nvml_loop, daemon=True)
+            self.t.start()
+            return self
         try:
+            self.first = threading.Event()
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
                                           "--format=csv,noheader,nounits", "-lms", "200"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
+            self.first.wait(5.0)
+            self.lines.clear()  # keep only samples taken once the region has opened
+            self.source = "nvidia-smi, every 200 ms"
         except Exception:
             self.proc = None
         return self
 
-    def _read(self):
-        for line in self.proc.stdout:
-            self.lines.append(line.strip())
-
     def __exit__(self, *a):
+        if self.nvml:
+            self.stop.set()
+            self.t.join(timeout=1.0)
+            self._nvml_sample()
+            return
         if self.proc:
             self.proc.terminate()
             try:
@@ -135,22 +225,27 @@ class ClockSampler:
                 self.proc.kill()
 
     def summary(self):
-        sm, mx, reasons = [], None, set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
-            parts = [x.strip() for x in ln.split(",")]
-            if len(parts) < 9:
-                continue
-            try:
-                sm.append(float(parts[1]))
-                mx = float(parts[2])
-            except ValueError:
-                continue
-            for nm, val in zip(names, parts[5:9]):
-                if val.lower().startswith("active"):
-                    reasons.add(nm)
+        sm, mx, reasons = [], self.max_mhz, set()
+        if self.nvml:
+            for mhz, bits in self.samples:
+                sm.append(mhz)
+                reasons |= {nm for nm, b in self.BITS.items() if bits & b}
+        else:
+            names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+            for ln in self.lines:
+                parts = [x.strip() for x in ln.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    mx = float(parts[2])
+                except ValueError:
+                    continue
+                for nm, val in zip(names, parts[5:9]):
+                    if val.lower().startswith("active"):
+                        reasons.add(nm)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm), "source": self.source}
 
 
 def _dist():
@@ -709,6 +804,8 @@ def main():
     ap.add_argument("--no-modes", action="store_true", help="only the headline configuration")
     args = ap.parse_args()
     world, rank, local = _dist()
+    if args.impl != "reference" and torch.cuda.is_available():
+        ClockSampler.open_nvml(local)  # before any warm-up
     if args.impl == "reference":
         run_reference(args, world, rank)
     elif args.workload == "batched":

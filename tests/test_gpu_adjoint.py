@@ -101,7 +101,7 @@ def test_autograd_function():
     J = (0.5 * m2 / UN[0]).sum() * prob.cell_volume()
     J.backward()
     Jo, _, lam0, dxi = adj.adjoint_run(U, prob, 5, dt, 2)
-    assert float(J) == pytest.approx(Jo, rel=1e-12)
+    assert float(J.detach()) == pytest.approx(Jo, rel=1e-12)
     assert close(U0.grad.cpu(), lam0, 1e-9)
     assert float(xi.grad) == pytest.approx(dxi, rel=1e-8)
     s.close()

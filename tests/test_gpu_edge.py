@@ -100,3 +100,47 @@ def test_full_batched_workload_sampled_runs():
         err = rel_linf(b.get_state(i, "cpu"), ro.run(U, prob, 1), w["gamma"])
         assert max(err) < 1e-5, (i, w["n"], w["xi"], err)
     b.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp64_df", "fp32_pert"])
+def test_zero_steps_and_rejected_calls_change_nothing(precision):
+    """step(0), and calls the library rejects (negative nsteps, non-finite dt),
+    launch no kernel and leave the state, the time and the next dt as they
+    were.  A float64 state comes back bit for bit from set/get."""
+    w = inputs.polytrope_2d(20, 24, xi=20.0, contrast=20.0, amp=1e-2)
+    s = rsst.Solver(w, precision)
+    U0 = torch.from_numpy(w["U"]).cuda()
+    s.set_state(U0)
+    before, dt0, n0 = s.get_state("cpu"), s.dt(), s.launches()
+    if precision == "fp64":
+        assert torch.equal(before, U0.cpu())
+    s.step(0)
+    for bad in [dict(nsteps=-1), dict(nsteps=1, dt=float("nan")), dict(nsteps=1, dt=float("inf"))]:
+        with pytest.raises(rsst.RsstError) as e:
+            s.step(**bad)
+        assert e.value.code == rsst.RSST_EINVAL
+    assert s.launches() == n0
+    assert torch.equal(s.get_state("cpu"), before)
+    assert s.time() == 0.0 and s.dt() == dt0
+    s.close()
+
+
+def test_batch_zero_steps_change_nothing():
+    ws = small_batch_runs()
+    b = rsst.BatchSolver(ws)
+    for i, w in enumerate(ws):
+        b.set_state(i, torch.from_numpy(w["U"]).cuda())
+    before = [b.get_state(i, "cpu") for i in range(len(ws))]
+    n0 = b.launches()
+    b.step(0)
+    b.step_looped(0)
+    with pytest.raises(rsst.RsstError):
+        b.step(-1)
+    assert b.launches() == n0
+    for i in range(len(ws)):
+        assert torch.equal(b.get_state(i, "cpu"), before[i])
+    b.close()
+
+
+def small_batch_runs():
+    return inputs.batched_runs(count=3, seed=4, max_size=40)
