@@ -201,8 +201,12 @@ static int build_descriptors(rsst_batch* b, int c) {
     return RSST_ECUDA;
   }
   int per_sm = 0, dev = 0, sms = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) {
+    cudaGetLastError();
+    rsst_set_error("rsst_batch: cannot query the device's SM count");
+    return RSST_ECUDA;
+  }
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, nt, smem) != cudaSuccess || per_sm < 1) per_sm = 1;
   b->grid = sms * per_sm < total ? sms * per_sm : total;
   if (b->grid < 1) b->grid = 1;
@@ -243,7 +247,10 @@ static int capture_graphs(rsst_batch* b) {
     int rc = launch_stage(b, 1, p);
     if (rc == RSST_OK) rc = launch_stage(b, 2, p);
     const cudaError_t e = cudaStreamEndCapture(b->stream, &g);
-    if (rc != RSST_OK) return rc;
+    if (rc != RSST_OK) {
+      if (g) cudaGraphDestroy(g);
+      return rc;
+    }
     if (e != cudaSuccess || cudaGraphInstantiate(&b->graph[p], g, 0) != cudaSuccess) {
       if (g) cudaGraphDestroy(g);
       rsst_set_error("graph capture of the batch step failed");
@@ -417,6 +424,12 @@ extern "C" int rsst_batch_autotune(rsst_batch* b, int steps, int32_t* choice_out
   std::vector<void*> save(b->nruns, nullptr);
   std::vector<double*> ssave(b->nruns, nullptr);
   int rc = RSST_OK;
+  auto ck = [&rc](cudaError_t e, const char* what) {
+    if (e != cudaSuccess && rc == RSST_OK) {
+      rsst_set_error("rsst_batch_autotune: %s: %s", what, cudaGetErrorString(e));
+      rc = RSST_ECUDA;
+    }
+  };
   for (int i = 0; i < b->nruns && rc == RSST_OK; ++i) {
     rsst_handle* h = b->runs[i];
     const size_t bytes = (size_t)(h->g.ndim + 2) * h->g.fstride * h->elem;
@@ -426,41 +439,44 @@ extern "C" int rsst_batch_autotune(rsst_batch* b, int steps, int32_t* choice_out
       rc = RSST_ENOMEM;
       break;
     }
-    cudaMemcpyAsync(save[i], h->buf[0], bytes, cudaMemcpyDeviceToDevice, b->stream);
-    cudaMemcpyAsync(ssave[i], h->d_scal, 16 * sizeof(double), cudaMemcpyDeviceToDevice, b->stream);
+    ck(cudaMemcpyAsync(save[i], h->buf[0], bytes, cudaMemcpyDeviceToDevice, b->stream), "state backup");
+    ck(cudaMemcpyAsync(ssave[i], h->d_scal, 16 * sizeof(double), cudaMemcpyDeviceToDevice, b->stream), "scalar backup");
   }
   const int slot0 = b->slot;
   double best_ms = 1e30;
   int best = 0;
-  cudaEvent_t e0, e1;
-  cudaEventCreate(&e0);
-  cudaEventCreate(&e1);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  ck(cudaEventCreate(&e0), "event");
+  ck(cudaEventCreate(&e1), "event");
   for (int c = 0; c < NCAND && rc == RSST_OK; ++c) {
-    rc = build_descriptors(b, c);
-    if (rc != RSST_OK) break;
-    b->slot = slot0;
-    rc = rsst_batch_step(b, 1);  // warm-up (and graph capture)
-    if (rc != RSST_OK) break;
-    cudaEventRecord(e0, b->stream);
-    rc = rsst_batch_step(b, steps);
-    cudaEventRecord(e1, b->stream);
-    cudaEventSynchronize(e1);
-    float ms = 0.0f;
-    cudaEventElapsedTime(&ms, e0, e1);
-    if (ms < best_ms) {
-      best_ms = ms;
-      best = c;
+    int rt = build_descriptors(b, c);
+    if (rt == RSST_OK) {
+      b->slot = slot0;
+      rt = rsst_batch_step(b, 1);  // warm-up (and graph capture)
     }
-    for (int i = 0; i < b->nruns; ++i) {  // restore
+    if (rt == RSST_OK) {
+      ck(cudaEventRecord(e0, b->stream), "event record");
+      rt = rsst_batch_step(b, steps);
+      ck(cudaEventRecord(e1, b->stream), "event record");
+      ck(cudaEventSynchronize(e1), "event wait");
+      float ms = 0.0f;
+      ck(cudaEventElapsedTime(&ms, e0, e1), "event time");
+      if (rt == RSST_OK && rc == RSST_OK && ms < best_ms) {
+        best_ms = ms;
+        best = c;
+      }
+    }
+    if (rt != RSST_OK && rc == RSST_OK) rc = rt;
+    for (int i = 0; i < b->nruns; ++i) {  // restore, also after a failed trial
       rsst_handle* h = b->runs[i];
       const size_t bytes = (size_t)(h->g.ndim + 2) * h->g.fstride * h->elem;
-      cudaMemcpyAsync(h->buf[0], save[i], bytes, cudaMemcpyDeviceToDevice, b->stream);
-      cudaMemcpyAsync(h->d_scal, ssave[i], 16 * sizeof(double), cudaMemcpyDeviceToDevice, b->stream);
+      ck(cudaMemcpyAsync(h->buf[0], save[i], bytes, cudaMemcpyDeviceToDevice, b->stream), "state restore");
+      ck(cudaMemcpyAsync(h->d_scal, ssave[i], 16 * sizeof(double), cudaMemcpyDeviceToDevice, b->stream), "scalar restore");
     }
   }
-  cudaStreamSynchronize(b->stream);
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
+  ck(cudaStreamSynchronize(b->stream), "stream wait");
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
   for (int i = 0; i < b->nruns; ++i) {
     cudaFree(save[i]);
     cudaFree(ssave[i]);

@@ -76,8 +76,12 @@ extern "C" int rsst_math_selftest(int32_t n, double* rcp_max_ulp, int32_t* mc_mi
     rsst_set_error("rsst_math_selftest: allocation failed");
     return RSST_ENOMEM;
   }
-  cudaMemset(d_ulp, 0, 2 * sizeof(*d_ulp));
-  cudaMemset(d_bad, 0, sizeof(*d_bad));
+  if (cudaMemset(d_ulp, 0, 2 * sizeof(*d_ulp)) != cudaSuccess || cudaMemset(d_bad, 0, sizeof(*d_bad)) != cudaSuccess) {
+    cudaFree(d_ulp);
+    cudaFree(d_bad);
+    rsst_set_error("rsst_math_selftest: memset failed");
+    return RSST_ECUDA;
+  }
   rsst::selftest_kernel<<<(n + 255) / 256, 256>>>(n, d_ulp, d_bad, d_ulp + 1);
   unsigned long long ulp[2] = {0, 0};
   unsigned int bad = 0;
