@@ -77,3 +77,32 @@ def test_entropy_wave_converges_at_second_order(variant, xi):
     err = [_entropy_wave_error(n, variant, xi) for n in (64, 128, 256)]
     orders = [math.log2(err[i] / err[i + 1]) for i in range(2)]
     assert orders[0] > 1.8 and orders[1] > 1.9, (err, orders)
+
+
+def _entropy_wave_2d_error(axis, variant=ro.EULER, xi=1.0, n=64, m=8):
+    """Entropy wave along `axis` on a grid whose cells are 16 times longer
+    along the other axis (n cells on [0, 1], m cells on [0, 2])."""
+    gamma = 1.4
+    nx, ny = (n, m) if axis == 0 else (m, n)
+    Lx, Ly = (1.0, 2.0) if axis == 0 else (2.0, 1.0)
+    t = (torch.arange(n, dtype=DT) + 0.5) / n
+    prof = 1.0 + 0.2 * torch.sin(2.0 * math.pi * t)
+    rho = (prof[None, :].expand(ny, nx) if axis == 0 else prof[:, None].expand(ny, nx)).contiguous()
+    vx, vy = (1.0, 0.0) if axis == 0 else (0.0, 1.0)
+    U0 = torch.stack([rho, rho * vx, rho * vy, 1.0 / (gamma - 1) + 0.5 * rho * (vx * vx + vy * vy)])
+    prob = ro.Problem(ndim=2, n=(nx, ny), dx=(Lx / nx, Ly / ny), gamma=gamma, xi=xi, variant=variant,
+                      bc=(ro.PERIODIC, ro.PERIODIC), cfl=0.4, vertical=-1, bg_rho=None, bg_p=None, cmax=None)
+    steps = math.ceil(1.0 / ro.cfl_dt(U0, prob))
+    U = ro.run(U0, prob, steps, dt=1.0 / steps)
+    return float((U[0] - U0[0]).abs().mean())
+
+
+@pytest.mark.parametrize("variant,xi", [(ro.EULER, 1.0), (ro.PVS, 5.0)])
+def test_entropy_wave_on_an_anisotropic_grid(variant, xi):
+    """Each axis's flux difference is divided by that axis's cell width: the
+    wave comes back after one period along x and along y alike (a width
+    taken from the other axis moves it 16 times too fast or too slow)."""
+    ex = _entropy_wave_2d_error(0, variant, xi)
+    ey = _entropy_wave_2d_error(1, variant, xi)
+    assert ex < 2e-3, ex
+    assert ey == pytest.approx(ex, rel=1e-9)
