@@ -100,7 +100,10 @@ typedef struct rsst_config {
   double cfl;          /* Courant number (0.4 in Sec. 4.2) */
   double grav[3];      /* constant acceleration F of App. B */
   int32_t vertical;    /* background axis, or -1 */
-  int32_t reserved;
+  int32_t cfl_rule;    /* 0: dt = cfl / max_cells sum_d c_tot/dx_d (default);
+                        * 1: dt = cfl min_d dx_d / max_cells c_tot (the paper
+                        * names only the Courant number, Sec. 4.2; in 1D the
+                        * two agree) */
   const double* bg_rho;
   const double* bg_p;
   double cmax;         /* > 0: state-dependent reduction xi = [1 + (a/cmax)^4]^(1/4)
@@ -115,7 +118,7 @@ typedef struct rsst_handle rsst_handle;
  * the current CUDA device; *h is NULL on failure and everything allocated is
  * freed.  `stream` is a cudaStream_t (may be NULL).  Errors: RSST_EINVAL for
  * an invalid config, checked before any device call (ndim, n, dx, bc, form,
- * precision, xi >= 1, gamma > 1, cfl > 0, cmax >= 0, finite gravity, the
+ * precision, xi >= 1, gamma > 1, cfl > 0, cfl_rule 0 or 1, cmax >= 0, finite gravity, the
  * background entries); RSST_ENOMEM when an allocation fails; RSST_ECUDA
  * when a copy, kernel or tensor-map encoding fails.  Synchronous. */
 int rsst_init(rsst_handle** h, const rsst_config* cfg, void* stream);
@@ -136,7 +139,8 @@ int rsst_set_state(rsst_handle* h, const double* U, int on_host);
 int rsst_get_state(rsst_handle* h, double* U, int on_host);
 
 /* Advance nsteps SSP-RK2 steps (Sec. 4.2).  dt > 0: fixed step.  dt <= 0:
- * each step takes dt = cfl / max_cells sum_d c_tot/dx_d from the state at
+ * each step takes dt = cfl / max_cells sum_d c_tot/dx_d (cfl_rule 0; with
+ * cfl_rule 1, cfl min_d dx_d / max_cells c_tot) from the state at
  * its start, entirely on the device.  Each step is two fused stage kernels
  * (reconstruction, LLF flux, divergence, RSST correction, force, RK update,
  * ghost cells; the second also reduces the CFL maximum).  Whole blocks of

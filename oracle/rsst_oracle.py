@@ -84,6 +84,7 @@ class Problem:
     bg_rho: Optional[torch.Tensor] = None
     bg_p: Optional[torch.Tensor] = None
     cmax: Optional[float] = None  # C_max law (Eq. cx) instead of a constant xi
+    cfl_rule: int = 0  # 0: dt = C / max sum_d c_tot/dx_d;  1: dt = C min_d dx_d / max c_tot (reading 3)
 
     @property
     def nvar(self) -> int:
@@ -366,9 +367,12 @@ def rhs(U: torch.Tensor, prob: Problem) -> torch.Tensor:
 
 def cfl_dt(U: torch.Tensor, prob: Problem) -> float:
     """dt = C / max_cells sum_d c_tot / dx_d with C = prob.cfl (Courant
-    number 0.4 of Sec. 4.2; the multi-dimensional sum is reading 3)."""
+    number 0.4 of Sec. 4.2; the multi-dimensional sum is reading 3), or with
+    prob.cfl_rule = 1 the other reading, dt = C min_d dx_d / max_cells c_tot."""
     with torch.no_grad():
         c = c_tot(U, prob.gamma, float(prob.xi), prob.cmax)
+        if prob.cfl_rule == 1:
+            return float(prob.cfl * min(float(prob.dx[d]) for d in range(prob.ndim)) / c.max())
         rate = sum(c / prob.dx[d] for d in range(prob.ndim))
         return float(prob.cfl / rate.max())
 

@@ -22,6 +22,7 @@ def problem_from(w: dict, **over):
         bg_rho=None if w["bg_rho"] is None else torch.as_tensor(w["bg_rho"], dtype=ro.DT),
         bg_p=None if w["bg_p"] is None else torch.as_tensor(w["bg_p"], dtype=ro.DT),
         cmax=w.get("cmax") or None,
+        cfl_rule=int(w.get("cfl_rule", 0)),
     )
     if over:
         if "variant" in over and isinstance(over["variant"], str):

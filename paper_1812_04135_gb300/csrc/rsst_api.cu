@@ -128,6 +128,7 @@ static int validate(const rsst_config* c) {
   if (!(c->xi >= 1.0) || !std::isfinite(c->xi)) { rsst_set_error("xi must be finite and >= 1 (got %g)", c->xi); return RSST_EINVAL; }
   if (!(c->gamma > 1.0) || !std::isfinite(c->gamma)) { rsst_set_error("gamma must be finite and > 1"); return RSST_EINVAL; }
   if (!(c->cfl > 0.0) || !std::isfinite(c->cfl)) { rsst_set_error("cfl must be finite and > 0"); return RSST_EINVAL; }
+  if (c->cfl_rule != 0 && c->cfl_rule != 1) { rsst_set_error("cfl_rule must be 0 or 1 (got %d)", c->cfl_rule); return RSST_EINVAL; }
   for (int d = 0; d < c->ndim; ++d)
     if (!std::isfinite(c->grav[d])) { rsst_set_error("grav[%d] must be finite", d); return RSST_EINVAL; }
   if (!(c->cmax >= 0.0) || !std::isfinite(c->cmax)) { rsst_set_error("cmax must be >= 0 (0: constant xi)"); return RSST_EINVAL; }
@@ -203,6 +204,13 @@ static void make_phys(const rsst_config* c, Phys* p) {
     p->bc[d] = act ? c->bc[d] : RSST_BC_PERIODIC;
     if (act) p->sum_inv_dx += 1.0 / c->dx[d];
     if (act && c->grav[d] != 0.0) p->has_grav = 1;
+  }
+  // Every kernel forms the CFL rate as c_tot * sum_inv_dx; the rule
+  // dt = cfl min_d dx_d / max c_tot is the same with 1 / min_d dx_d.
+  if (c->cfl_rule == 1) {
+    double m = 0.0;
+    for (int d = 0; d < c->ndim; ++d) m = std::fmax(m, 1.0 / c->dx[d]);
+    p->sum_inv_dx = m;
   }
 }
 

@@ -91,7 +91,8 @@ def test_periodic_background_ghost_entries_are_not_read(L):
         rsst.rsst_destroy(h)
 
 
-@pytest.mark.parametrize("field,value", [("grav", float("inf")), ("gamma", float("inf")), ("cfl", float("nan"))])
+@pytest.mark.parametrize("field,value", [("grav", float("inf")), ("gamma", float("inf")), ("cfl", float("nan")),
+                                         ("cfl_rule", 2), ("cfl_rule", -1)])
 def test_non_finite_parameters_rejected_without_gpu(L, field, value):
     kw = dict(variant="pvs", xi=3.0)
     kw[field] = (0.0, value, 0.0) if field == "grav" else value

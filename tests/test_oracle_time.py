@@ -21,10 +21,11 @@ from oracle import rsst_oracle as ro
 DT = torch.float64
 
 
-def problem(n, dx, xi=1.0, variant=ro.EULER, gamma=1.4):
+def problem(n, dx, xi=1.0, variant=ro.EULER, gamma=1.4, cfl_rule=0):
     nd = len(n)
     return ro.Problem(ndim=nd, n=tuple(n), dx=tuple(dx), gamma=gamma, xi=xi, variant=variant, grav=(0.0, 0.0, 0.0),
-                      bc=(ro.PERIODIC,) * nd, cfl=0.4, vertical=-1, bg_rho=None, bg_p=None, cmax=None)
+                      bc=(ro.PERIODIC,) * nd, cfl=0.4, vertical=-1, bg_rho=None, bg_p=None, cmax=None,
+                      cfl_rule=cfl_rule)
 
 
 def uniform(n, rho, vel, p, gamma=1.4):
@@ -44,6 +45,22 @@ def test_cfl_is_the_acoustic_courant_condition_at_rest(n, dx, xi):
     a = math.sqrt(gamma * p / rho)
     courant = (a / xi) * dt * sum(1.0 / h for h in dx)
     assert courant == pytest.approx(0.4, rel=1e-13)
+
+
+@pytest.mark.parametrize("n,dx", [((16,), (0.1,)), ((8, 6), (0.1, 0.03)), ((4, 5, 6), (0.2, 0.05, 0.01))])
+def test_min_width_cfl_rule_at_rest(n, dx):
+    """The other reading of the multi-dimensional CFL step: (a/xi) dt / min dx = C;
+    in 1D it is the same step as the sum rule."""
+    gamma, rho, p, xi = 1.4, 1.7, 0.9, 7.0
+    U = uniform(n, rho, (0.0,) * len(n), p, gamma)
+    dt = ro.cfl_dt(U, problem(n, dx, xi=xi, gamma=gamma, cfl_rule=1))
+    a = math.sqrt(gamma * p / rho)
+    assert (a / xi) * dt / min(dx) == pytest.approx(0.4, rel=1e-13)
+    dt0 = ro.cfl_dt(U, problem(n, dx, xi=xi, gamma=gamma))
+    if len(n) == 1:
+        assert dt == pytest.approx(dt0, rel=1e-14)
+    else:
+        assert dt > dt0
 
 
 def test_cfl_scales_with_speeds_and_lengths():
