@@ -205,6 +205,19 @@ int rsst_adjoint_step(rsst_handle* h, int32_t seg, double* lam, double* dJ_dxi);
  * (-|V|^2/2, V, 0) * cell volume).  Float64 runs.  Synchronous. */
 int rsst_kinetic_energy(rsst_handle* h, double* J, double* grad);
 
+/* Density gradient at fixed velocity and pressure from a conserved-state
+ * gradient (an option of this library's adjoint conventions; the paper has
+ * no adjoint): with m = rho V and E = P/(gamma-1) + rho |V|^2/2,
+ *   out = dJ/drho|_{V,P} = lam_rho + V . lam_m + |V|^2/2 lam_E
+ * per cell, V from U.  U: the state the gradient refers to (the initial
+ * state for rsst_adjoint_step's result), lam: dJ/dU, both device pointers,
+ * float64, caller layout [ndim+2][nz][ny][nx] (no ghosts); out: device,
+ * ncells float64; n: host array of ndim interior sizes.  Asynchronous on
+ * `stream` (cudaStream_t, may be NULL).  RSST_EINVAL for NULL or host
+ * pointers, ndim outside 1..3, n[d] < 1 or more than 2^31 cells. */
+int rsst_adjoint_rho_fixed_vp(const double* U, const double* lam, double* out, int32_t ndim, const int32_t* n,
+                              void* stream);
+
 /* ---- Batched runs (one persistent kernel per RK stage for all runs) ------
  * Many independent 2D RSST_FP32_PERT runs (vertical axis y or none) of
  * uneven size, xi and background, advanced together (the method of Sec. 4.2

@@ -78,3 +78,17 @@ def adjoint_run(U0: torch.Tensor, prob: ro.Problem, nsteps: int, dt: float, ever
         lam = gU.detach()
         dxi += 0.0 if gxi is None else float(gxi)
     return J, U, lam, dxi
+
+
+def rho_gradient_fixed_vp(U0: torch.Tensor, lam0: torch.Tensor, gamma) -> torch.Tensor:
+    """Density gradient at fixed velocity and pressure from the conserved-state
+    gradient (the optional chain rule of the adjoint readings): with
+    m = rho V and E = e(rho, P) + rho |V|^2/2,
+    dJ/drho|_{V,P} = lam_rho + V . lam_m + [(de/drho)_P + |V|^2/2] lam_E."""
+    eos = ro.as_eos(gamma)
+    rho, V, v2, P, a2 = ro.primitives(U0, eos)
+    nd = U0.shape[0] - 2
+    out = lam0[0] + (eos.de_drho(rho, P) + 0.5 * v2) * lam0[-1]
+    for d in range(nd):
+        out = out + V[d] * lam0[1 + d]
+    return out

@@ -849,3 +849,53 @@ extern "C" int rsst_kinetic_energy(rsst_handle* h, double* J, double* grad) {
   h->launches += 2;
   return rc;
 }
+
+namespace rsst {
+
+// dJ/drho at fixed V and P from dJ/dU (ideal gas, (de/drho)_P = 0):
+// lam_rho + V . lam_m + |V|^2/2 lam_E, cell by cell; caller layout, planes of
+// `cells` values.
+template <int NV>
+__global__ void rho_fixed_vp_kernel(const double* __restrict__ U, const double* __restrict__ lam,
+                                    double* __restrict__ out, int64_t cells) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < cells; i += (int64_t)gridDim.x * blockDim.x) {
+    const double rho = U[i];
+    double acc = lam[i], v2 = 0.0;
+#pragma unroll
+    for (int d = 0; d < NV - 2; ++d) {
+      const double v = U[(1 + d) * cells + i] / rho;
+      acc = fma(v, lam[(1 + d) * cells + i], acc);
+      v2 = fma(v, v, v2);
+    }
+    out[i] = fma(0.5 * v2, lam[(NV - 1) * cells + i], acc);
+  }
+}
+
+}  // namespace rsst
+
+extern "C" int rsst_adjoint_rho_fixed_vp(const double* U, const double* lam, double* out, int32_t ndim,
+                                         const int32_t* n, void* stream) {
+  if (!U || !lam || !out || !n || ndim < 1 || ndim > 3) {
+    rsst_set_error("rsst_adjoint_rho_fixed_vp: NULL pointer or ndim outside 1..3");
+    return RSST_EINVAL;
+  }
+  int64_t cells = 1;
+  for (int d = 0; d < ndim; ++d) {
+    if (n[d] < 1) { rsst_set_error("rsst_adjoint_rho_fixed_vp: n[%d] < 1", d); return RSST_EINVAL; }
+    cells *= n[d];
+  }
+  if (cells > (int64_t)1 << 31) { rsst_set_error("rsst_adjoint_rho_fixed_vp: grid too large"); return RSST_EINVAL; }
+  if (rsst_check_buffer(U, 0, "rsst_adjoint_rho_fixed_vp (U)") != RSST_OK ||
+      rsst_check_buffer(lam, 0, "rsst_adjoint_rho_fixed_vp (lam)") != RSST_OK ||
+      rsst_check_buffer(out, 0, "rsst_adjoint_rho_fixed_vp (out)") != RSST_OK)
+    return RSST_EINVAL;
+  const int64_t want = (cells + 255) / 256;
+  const int grid = (int)(want < 152 * 8 ? want : 152 * 8);
+  cudaStream_t st = (cudaStream_t)stream;
+  switch (ndim) {
+    case 1: rsst::rho_fixed_vp_kernel<3><<<grid, 256, 0, st>>>(U, lam, out, cells); break;
+    case 2: rsst::rho_fixed_vp_kernel<4><<<grid, 256, 0, st>>>(U, lam, out, cells); break;
+    default: rsst::rho_fixed_vp_kernel<5><<<grid, 256, 0, st>>>(U, lam, out, cells); break;
+  }
+  return launch_err("rsst_adjoint_rho_fixed_vp");
+}

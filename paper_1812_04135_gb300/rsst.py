@@ -69,6 +69,7 @@ def lib():
             "rsst_adjoint_segments": (i32, [vp, C.POINTER(C.c_int32)]),
             "rsst_adjoint_step": (i32, [vp, i32, vp, pd]),
             "rsst_kinetic_energy": (i32, [vp, pd, vp]),
+            "rsst_adjoint_rho_fixed_vp": (i32, [vp, vp, vp, i32, C.POINTER(C.c_int32), vp]),
             "rsst_batch_init": (i32, [C.POINTER(vp), i32, C.POINTER(Config), vp]),
             "rsst_batch_destroy": (None, [vp]),
             "rsst_batch_set_state": (i32, [vp, i32, vp, i32]),
@@ -240,6 +241,20 @@ def rsst_adjoint_step(h: int, seg: int, lam) -> float:
     ptr = _f64_ptr(lam, "rsst_adjoint_step")
     _check(lib().rsst_adjoint_step(h, int(seg), ptr, C.byref(acc)), "rsst_adjoint_step")
     return acc.value
+
+
+def rsst_adjoint_rho_fixed_vp(U, lam, out, stream=None) -> None:
+    """dJ/drho at fixed V and P into ``out`` (float64 CUDA tensor of the grid's
+    shape) from ``lam`` = dJ/dU and the state ``U`` (float64 CUDA tensors,
+    caller layout [nvar][nz][ny][nx])."""
+    ndim = U.dim() - 1
+    if U.shape[0] != ndim + 2 or tuple(lam.shape) != tuple(U.shape) or tuple(out.shape) != tuple(U.shape[1:]):
+        raise ValueError(f"rsst_adjoint_rho_fixed_vp: shapes {tuple(U.shape)}, {tuple(lam.shape)}, {tuple(out.shape)}")
+    n = (C.c_int32 * ndim)(*[int(U.shape[ndim - d]) for d in range(ndim)])  # (x, y, z) order
+    pu = _f64_ptr(U, "rsst_adjoint_rho_fixed_vp")
+    pl = _f64_ptr(lam, "rsst_adjoint_rho_fixed_vp")
+    po = _f64_ptr(out, "rsst_adjoint_rho_fixed_vp")
+    _check(lib().rsst_adjoint_rho_fixed_vp(pu, pl, po, ndim, n, _stream_ptr(stream)), "rsst_adjoint_rho_fixed_vp")
 
 
 def rsst_kinetic_energy(h: int, grad=None) -> float:

@@ -127,3 +127,17 @@ def test_binding_rejects_wrong_buffers_before_the_library():
         rsst.rsst_set_state(0, torch.zeros(4, 4, dtype=torch.float64).t(), on_host=True)  # not contiguous
     with pytest.raises(ValueError):
         rsst.rsst_adjoint_step(0, 0, torch.zeros(8, dtype=torch.float64))                 # must be a CUDA tensor
+
+
+def test_rho_fixed_vp_rejects_bad_arguments_without_gpu(L):
+    import ctypes as C
+    import torch
+    n = (C.c_int32 * 2)(4, 3)
+    assert L.rsst_adjoint_rho_fixed_vp(None, None, None, 2, n, None) == rsst.RSST_EINVAL
+    assert L.rsst_adjoint_rho_fixed_vp(None, None, None, 4, n, None) == rsst.RSST_EINVAL
+    with pytest.raises(ValueError):   # host tensors
+        rsst.rsst_adjoint_rho_fixed_vp(torch.zeros(4, 3, 4, dtype=torch.float64), torch.zeros(4, 3, 4, dtype=torch.float64),
+                                       torch.zeros(3, 4, dtype=torch.float64))
+    with pytest.raises(ValueError):   # shape mismatch
+        rsst.rsst_adjoint_rho_fixed_vp(torch.zeros(4, 3, 4, dtype=torch.float64), torch.zeros(4, 3, 5, dtype=torch.float64),
+                                       torch.zeros(3, 4, dtype=torch.float64))

@@ -202,3 +202,27 @@ def test_one_step_vjp_cmax(var):
     _, got, dxi = gpu_adjoint(w, dt, 1, 1, lam)
     assert close(got, gU, 1e-10)
     assert dxi == 0.0
+
+
+@pytest.mark.parametrize("name,make", CASES)
+def test_density_gradient_at_fixed_velocity_and_pressure(name, make):
+    """rsst_adjoint_rho_fixed_vp on the device against the oracle's chain rule:
+    on the same gradient (the kernel alone, to rounding), and on the GPU
+    adjoint's gradient against the oracle adjoint's (the whole chain)."""
+    w = make()
+    prob, U = problem_from(w)
+    U = ro.run(U, prob, 2)  # some motion, so V . lam_m and |V|^2 lam_E matter
+    w = dict(w)
+    w["U"] = U.numpy().copy()
+    dt = ro.cfl_dt(U, prob)
+    J, UN, lam0, dxi = adj.adjoint_run(U, prob, 5, dt, 2)
+    want = adj.rho_gradient_fixed_vp(U, lam0, prob.gamma)
+    Ud, ld = U.cuda().contiguous(), lam0.cuda().contiguous()
+    out = torch.empty(tuple(U.shape[1:]), dtype=torch.float64, device="cuda")
+    rsst.rsst_adjoint_rho_fixed_vp(Ud, ld, out)
+    torch.cuda.synchronize()
+    assert close(out.cpu(), want, 1e-14)
+    _, glam, _ = gpu_adjoint(w, dt, 5, 2, ro.kinetic_energy_gradient(UN, prob))
+    rsst.rsst_adjoint_rho_fixed_vp(Ud, glam.cuda().contiguous(), out)
+    torch.cuda.synchronize()
+    assert close(out.cpu(), want, 1e-9)

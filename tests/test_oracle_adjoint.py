@@ -57,3 +57,33 @@ def test_dot_product_identity():
     lhs = float((lam * Jv).sum())
     rhs = float((JTlam * v).sum())
     assert lhs == pytest.approx(rhs, rel=1e-12)
+
+
+def test_density_gradient_at_fixed_velocity_and_pressure():
+    """The chain rule of the conserved-state gradient to a density change at
+    fixed V and P, against central differences of J over such changes."""
+    prob, U0, dt = _case()
+    nsteps, every = 4, 2
+    J, UN, lam, dxi = adj.adjoint_run(U0, prob, nsteps, dt, every)
+    g = adj.rho_gradient_fixed_vp(U0, lam, prob.gamma)
+    rho, V, v2, P, a2 = ro.primitives(U0, prob.gamma)
+
+    def at_rho(j, i, r):
+        U = U0.clone()
+        vx, vy = float(V[0][j, i]), float(V[1][j, i])
+        U[0, j, i] = r
+        U[1, j, i] = r * vx
+        U[2, j, i] = r * vy
+        U[3, j, i] = float(P[j, i]) / (prob.gamma - 1.0) + 0.5 * r * (vx * vx + vy * vy)
+        return U
+
+    for (j, i) in [(3, 5), (0, 0), (15, 11), (8, 2)]:
+        r0 = float(rho[j, i])
+        h = 1e-6 * r0
+        fd = (_J(at_rho(j, i, r0 + h), prob, nsteps, dt) - _J(at_rho(j, i, r0 - h), prob, nsteps, dt)) / (2 * h)
+        assert float(g[j, i]) == pytest.approx(fd, rel=2e-5, abs=1e-9 * abs(J) / h), (j, i)
+    # at V = 0 it is the fixed-(m, E) gradient plus (de/drho)_P lam_E, which is 0 for an ideal gas
+    Z = U0.clone()
+    Z[1:3] = 0.0
+    Z[3] = P / (prob.gamma - 1.0)
+    assert torch.equal(adj.rho_gradient_fixed_vp(Z, lam, prob.gamma), lam[0])
