@@ -88,3 +88,45 @@ def test_rt_growth_reduced_forms_track_the_unreduced_run():
     with pytest.raises(rsst.RsstError) as e:
         _vy_history("dvs", 10.0, (0.4,))
     assert e.value.code == rsst.RSST_ENONPHYSICAL
+
+
+def _vy_history_at(var, xi, times, n, precision="fp32_pert"):
+    """max|V_y| at exactly the given times (adaptive steps, the last one of
+    each interval shortened to land on the time)."""
+    w = inputs.rayleigh_taylor_2d(n, xi=xi, variant=var)
+    s = rsst.Solver(w, precision)
+    s.set_state(torch.from_numpy(w["U"]).cuda())
+    out = []
+    for T in times:
+        while True:
+            rem = T - s.time()
+            if rem <= 1e-12 * T:
+                break
+            dt = s.dt()
+            if dt >= rem:
+                s.step(1, rem)
+                break
+            s.step(max(1, min(int(rem / dt) - 1, 256)))
+        U = s.get_state("cuda")
+        out.append(float((U[2] / U[0]).abs().max()))
+    s.close()
+    return out
+
+
+@pytest.mark.slow
+def test_rt_growth_at_1024():
+    """The same comparison at 1024^2 (float32 perturbation; the xi = 1 run
+    takes ~3e5 steps to t = 1.6, xi = 10 ~3e4): the pressure-reduced forms
+    track the unreduced run within the same bounds as at 128^2."""
+    times = (0.4, 0.8, 1.2, 1.6)
+    ref = _vy_history_at("euler", 1.0, times, 1024)
+    runs = {(var, xi): _vy_history_at(var, xi, times, 1024) for var, xi in (("pvs", 10.0), ("pms", 10.0), ("pvs", 3.0))}
+    print("\n1024^2 max|V_y|(t) at t =", times)
+    print("  euler xi=1 :", " ".join("%.4f" % v for v in ref))
+    for (var, xi), h in runs.items():
+        print(f"  {var:5s} xi={xi:g}:", " ".join("%.4f" % v for v in h))
+    assert ref[-1] > 20 * ref[0]
+    for (var, xi), h in runs.items():
+        tol = 0.15 if xi > 5 else 0.08
+        for r, v in zip(ref, h):
+            assert abs(v - r) < tol * r, (var, xi, r, v)
