@@ -66,7 +66,8 @@ typedef enum {
 typedef enum {
   RSST_FP64 = 0,      /* state stored and computed in float64 (the two square
                        * roots of c_tot, which only set the LLF dissipation
-                       * and dt, to 2^-40 relative) */
+                       * and dt, to 2^-40 relative; the LLF speed as a
+                       * float pair on the float32 pipe) */
   RSST_FP32_PERT = 1, /* float32 perturbation about a float64 background */
   RSST_FP64_DF = 2    /* double-float: state stored and computed as pairs of
                        * float32 (hi + lo, 48-bit significand) on the float32
@@ -286,14 +287,16 @@ int64_t rsst_kernel_launches(const rsst_handle* h);
 
 /* Self-test of the float64 helpers the kernels use in place of compiler
  * sequences (no counterpart in the paper): over n seeded inputs, the largest
- * difference in ulps between the Newton-Raphson reciprocal and CUDA's
- * correctly rounded 1.0/x (x in [2^-20, 2^20]); the number of inputs on
- * which the integer-pipe MC limiter differs from the direct float64 form
- * (plus 2^20 if the c_tot square root misses one of its special cases: 0
- * and subnormal -> 0, negative -> NaN); and the largest relative
- * difference between the c_tot square root and CUDA's sqrt (x in
- * [2^-200, 2^200]).  All outputs are host pointers.  Synchronous, current
- * device. */
+ * difference in ulps between the reciprocal (hardware seed and one
+ * third-order step) and CUDA's correctly rounded 1.0/x (x in [2^-20, 2^20]);
+ * the number of inputs on which the integer-pipe MC limiter differs from
+ * the direct float64 form (plus 2^20 if a c_tot square root misses one of
+ * its special cases: 0 and subnormal -> 0, negative and NaN -> NaN, or the
+ * float-to-double bit conversion a case); and the largest relative
+ * difference between either c_tot square root (the float64 one of the CFL
+ * rate and the adjoint, the float-pair one of the LLF speed) and CUDA's
+ * sqrt (x in [2^-200, 2^200]).  All outputs are host pointers.
+ * Synchronous, current device. */
 int rsst_math_selftest(int32_t n, double* rcp_max_ulp, int32_t* mc_mismatches, double* sqrt_max_rel);
 
 /* sizeof(rsst_config) as compiled into the library (binding check). */

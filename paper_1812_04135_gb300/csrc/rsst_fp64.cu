@@ -182,7 +182,7 @@ __device__ __forceinline__ void face_pass(const double* __restrict__ su, double*
 }
 
 template <int NDIM, int BX, int BY, int BZ, int NT>
-__global__ void __launch_bounds__(NT) stage_fp64_kernel(const StageArgs<double> a) {
+__global__ void __launch_bounds__(NT, NDIM == 3 ? 3 : 0) stage_fp64_kernel(const StageArgs<double> a) {
   using C = TileCfg<NDIM, BX, BY, BZ, NT>;
   constexpr int NV = C::NV;
   extern __shared__ double smem[];

@@ -76,6 +76,59 @@ __device__ __forceinline__ double sqrt_ctot(double x) {
   return be > 0 ? s : (ix >= 0 ? 0.0 : __longlong_as_double(0x7ff8000000000000ll));
 }
 
+// sqrt(x) as an unevaluated pair of floats s + c (relative error below
+// 2^-42), for the LLF speed, on the integer and float32 pipes only: x =
+// 2^(2k) y with y in [1, 4) read from the bit pattern, y = h + l with h its
+// leading 24 significant bits and l the other 29 (rounded to a float);
+// s = h rsqrt(h) and one Newton step c = (y - s^2) / (2 s) with s^2 split
+// exactly by an FMA (h - s^2 is exact: Sterbenz), then both scaled by 2^k.
+// Zero and subnormal x give 0, negative x and NaN give NaN, like sqrt_ctot;
+// 2^k is kept to the float range (x in [2^-252, 2^256), far outside any
+// physical speed^2).
+__device__ __forceinline__ void sqrt_pair(double x, float& s, float& c) {
+  const long long ix = __double_as_longlong(x);
+  const int be = (int)(ix >> 52);  // biased exponent for x >= 0, negative for x < 0
+  const int e = be - 1023;
+  const int odd = e & 1;
+  const float h = __int_as_float(((127 + odd) << 23) | (int)((ix >> 29) & 0x7fffff));
+  const float l = __uint2float_rn((unsigned)(ix & 0x1fffffff)) * __int_as_float((75 + odd) << 23);  // * 2^(odd-52)
+  const float r = rsqrtf(h);
+  const float s0 = h * r;
+  const float p = s0 * s0;
+  const float d = ((h - p) - fmaf(s0, s0, -p)) + l;
+  const float c0 = d * (0.5f * r);
+  const int k = (e - odd) >> 1;
+  const float sc = k < -126 ? 0.0f : (k > 127 ? __int_as_float(0x7f800000) : __int_as_float((127 + k) << 23));
+  const bool fin = be > 0 && be < 2047;
+  const float special = (ix >= 0 && be == 0) ? 0.0f : __int_as_float(0x7fc00000);
+  s = fin ? s0 * sc : special;
+  c = fin ? c0 * sc : special;
+}
+
+// A float as a double, on the integer pipe (subnormal floats read as 0).
+__device__ __forceinline__ double f2d_bits(float f) {
+  const unsigned b = __float_as_uint(f);
+  const unsigned E = (b >> 23) & 0xffu;
+  const unsigned long long sign = (unsigned long long)(b >> 31) << 63;
+  const unsigned long long ex = E == 0u ? 0ull : (E == 255u ? 0x7ffull : (unsigned long long)(E + 896u)) << 52;
+  const unsigned long long mant = E == 0u ? 0ull : (unsigned long long)(b & 0x7fffffu) << 29;
+  return __longlong_as_double((long long)(sign | ex | mant));
+}
+
+// c_tot = |V| + a/xi from |V|^2 and (a/xi)^2 as a normalised float pair
+// (h + l, |l| <= ulp(h)/2): both square roots by sqrt_pair, summed exactly
+// in the leading parts (two-sum), relative error below 2^-41.
+__device__ __forceinline__ void ctot_pair(double v2, double a2x, float& h, float& l) {
+  float sv, cv, sa, ca;
+  sqrt_pair(v2, sv, cv);
+  sqrt_pair(a2x, sa, ca);
+  const float t = sv + sa;
+  const float bv = t - sv;
+  const float lo = ((sv - (t - bv)) + (sa - bv)) + (cv + ca);
+  h = t + lo;
+  l = lo - (h - t);
+}
+
 // Effective sound speed a/xi from a^2 and the factor f = 1 - 1/xi^2: constant
 // xi, or the C_max law xi = [1 + (a/C_max)^4]^(1/4) (Eq. cx, Sec. 4.3), for
 // which a/xi = sqrt(a^2 / sqrt(w)) and f = 1 - 1/sqrt(w), w = 1 + a^4/C_max^4.
@@ -95,10 +148,12 @@ __device__ __forceinline__ double ctot_sound(const Phys& p, double rho, double P
 }
 
 // The Euler flux along dimension D, F, and the approximate RSST
-// characteristic speed c_tot = |V| + a/xi of one state (Eq. pvs_dt0; Sec. 4.2).
+// characteristic speed c_tot = |V| + a/xi of one state (Eq. pvs_dt0; Sec. 4.2)
+// as a float pair ch + cl: for a constant xi from ctot_pair on the float32
+// pipe, under the C_max law from the float64 form.
 template <int NV, int D>
 __device__ __forceinline__ void euler_flux(const double (&q)[NV], const Phys& p,
-                                           double (&F)[NV], double& c) {
+                                           double (&F)[NV], float& ch, float& cl) {
   constexpr int ND = NV - 2;
   const double rho = q[0];
   const double ir = rcp_nr(rho);
@@ -110,7 +165,13 @@ __device__ __forceinline__ void euler_flux(const double (&q)[NV], const Phys& p,
     v2 += v[e] * v[e];
   }
   const double P = Eos::pressure(p, rho, q[NV - 1], rho * v2);
-  c = sqrt_ctot(v2) + ctot_sound(p, rho, P, ir);
+  if (p.use_cmax) {
+    const double c = sqrt_ctot(v2) + ctot_sound(p, rho, P, ir);
+    ch = __double2float_rn(c);
+    cl = __double2float_rn(c - (double)ch);
+  } else {
+    ctot_pair(v2, Eos::sound2_over_xi2(p, rho, P, ir), ch, cl);
+  }
   F[0] = q[1 + D];
 #pragma unroll
   for (int e = 0; e < ND; ++e) F[1 + e] = (e == D) ? fma(q[1 + e], v[D], P) : q[1 + e] * v[D];
@@ -124,10 +185,12 @@ __device__ __forceinline__ void euler_flux(const double (&q)[NV], const Phys& p,
 template <int NV, int D>
 __device__ __forceinline__ void llf_flux_x2(const double (&qL)[NV], const double (&qR)[NV],
                                             const Phys& p, double (&G)[NV]) {
-  double FL[NV], FR[NV], cL, cR;
-  euler_flux<NV, D>(qL, p, FL, cL);
-  euler_flux<NV, D>(qR, p, FR, cR);
-  const double alpha = (cL >= cR) ? cL : cR;
+  double FL[NV], FR[NV];
+  float hL, lL, hR, lR;
+  euler_flux<NV, D>(qL, p, FL, hL, lL);
+  euler_flux<NV, D>(qR, p, FR, hR, lR);
+  const bool left = hL > hR || (hL == hR && lL >= lR);  // normalised pairs order like their values
+  const double alpha = f2d_bits(left ? hL : hR) + f2d_bits(left ? lL : lR);
 #pragma unroll
   for (int k = 0; k < NV; ++k) G[k] = fma(-alpha, qR[k] - qL[k], FL[k] + FR[k]);
 }

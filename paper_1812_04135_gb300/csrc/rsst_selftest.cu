@@ -55,8 +55,21 @@ __global__ void selftest_kernel(int n, unsigned long long* max_ulp, unsigned int
   if (mode == 7) xs = (1.0 + u1) * (1.0 + u1);
   const double rel = fabs(sqrt_ctot(xs) - sqrt(xs)) / sqrt(xs);
   atomicMax(sqrt_rel_bits, (unsigned long long)__double_as_longlong(rel));  // non-negative: bits order as values
+  // the float-pair square root of the LLF speed, read back as s + c
+  float ps, pc;
+  sqrt_pair(xs, ps, pc);
+  const double prel = fabs(((double)ps + (double)pc) - sqrt(xs)) / sqrt(xs);
+  atomicMax(sqrt_rel_bits, (unsigned long long)__double_as_longlong(prel));
   if (i == 0) {
-    const bool specials = sqrt_ctot(0.0) == 0.0 && sqrt_ctot(4.9e-324) == 0.0 && isnan(sqrt_ctot(-1.0));
+    float z0, z1, s0, s1, n0, n1, q0, q1;
+    sqrt_pair(0.0, z0, z1);
+    sqrt_pair(4.9e-324, s0, s1);
+    sqrt_pair(-1.0, n0, n1);
+    sqrt_pair(__longlong_as_double(0x7ff8000000000000ll), q0, q1);
+    const bool specials = sqrt_ctot(0.0) == 0.0 && sqrt_ctot(4.9e-324) == 0.0 && isnan(sqrt_ctot(-1.0)) &&
+                          z0 == 0.0f && z1 == 0.0f && s0 == 0.0f && s1 == 0.0f && isnan(n0) && isnan(q0) &&
+                          f2d_bits(1.5f) == 1.5 && f2d_bits(-0.25f) == -0.25 && f2d_bits(0.0f) == 0.0 &&
+                          f2d_bits(3.0e-39f) == 0.0 && isinf(f2d_bits(__int_as_float(0x7f800000)));
     if (!specials) atomicAdd(mc_bad, 1u << 20);
   }
 }
