@@ -4,7 +4,6 @@ unchanged (comments aside), the algorithmic bytes per cell-stage, the
 float64 peak from unit counts and clock, and the clock-record parsing that
 decides whether a run is kept."""
 import json
-import os
 
 import pytest
 
