@@ -64,3 +64,44 @@ def test_split_is_exact_to_float_rounding_of_the_tail():
         l = np.float64(F32(F32(ix & 0x1FFFFFFF) * F32(_float((75 + odd) << 23))))
         y = x * 2.0 ** -(e - odd)
         assert abs((h + l) - y) <= 2.0 ** -48 * y
+
+
+def _two_sum_pair(sv, cv, sa, ca):
+    t = F32(sv + sa)
+    bv = F32(t - sv)
+    lo = F32(F32(F32(sv - F32(t - bv)) + F32(sa - bv)) + F32(cv + ca))
+    h = F32(t + lo)
+    return h, F32(lo - F32(h - t))
+
+
+def _f2d_bits(f):
+    b = struct.unpack("<I", struct.pack("<f", float(f)))[0]
+    E = (b >> 23) & 0xFF
+    sign = (b >> 31) << 63
+    ex = 0 if E == 0 else ((0x7FF if E == 255 else E + 896) << 52)
+    mant = 0 if E == 0 else (b & 0x7FFFFF) << 29
+    return struct.unpack("<d", struct.pack("<Q", sign | ex | mant))[0]
+
+
+def test_llf_speed_pair_sum_max_and_conversion():
+    """c_tot = |V| + a/xi from the two float-pair roots (two-sum, normalised),
+    the larger of two sides picked by comparing pairs, and the pair turned
+    back into a double by bit assembly: within 2^-41 of the float64 value."""
+    rng = np.random.default_rng(9)
+    for _ in range(5000):
+        sides = []
+        for _side in range(2):
+            v2 = float(rng.uniform(0.0, 4.0)) * 10.0 ** rng.integers(-8, 3)
+            a2x = float(rng.uniform(0.01, 10.0))
+            sv, cv = sqrt_pair(v2, rng.uniform(-1, 1) * 2.0 ** -22)
+            sa, ca = sqrt_pair(a2x, rng.uniform(-1, 1) * 2.0 ** -22)
+            h, l = _two_sum_pair(F32(sv), F32(cv), F32(sa), F32(ca))
+            assert abs(float(l)) <= 0.5 * float(np.spacing(h))          # normalised
+            sides.append((h, l, np.sqrt(v2) + np.sqrt(a2x)))
+        (hL, lL, cL), (hR, lR, cR) = sides
+        left = hL > hR or (hL == hR and lL >= lR)
+        alpha = _f2d_bits(hL if left else hR) + _f2d_bits(lL if left else lR)
+        assert abs(alpha - max(cL, cR)) <= 2.0 ** -41 * max(cL, cR)
+    for f in (1.5, -0.25, 0.0, 3.0e-39, float("inf")):
+        want = 0.0 if f == 3.0e-39 else f
+        assert _f2d_bits(F32(f)) == want
