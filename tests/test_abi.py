@@ -141,3 +141,22 @@ def test_rho_fixed_vp_rejects_bad_arguments_without_gpu(L):
     with pytest.raises(ValueError):   # shape mismatch
         rsst.rsst_adjoint_rho_fixed_vp(torch.zeros(4, 3, 4, dtype=torch.float64), torch.zeros(4, 3, 5, dtype=torch.float64),
                                        torch.zeros(3, 4, dtype=torch.float64))
+
+
+def test_header_is_plain_c_and_matches_the_library(L, tmp_path):
+    """include/rsst.h compiles as strict C99 (the boundary is a C ABI: plain
+    pointers, sizes and enums), and a C program sees the same rsst_config
+    size as the library."""
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "use_header.c"
+    src.write_text('#include <stdio.h>\n#include "rsst.h"\n'
+                   'int main(void) { printf("%zu\\n", sizeof(rsst_config)); return 0; }\n')
+    exe = tmp_path / "use_header"
+    subprocess.run([gcc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-I", os.path.join(ROOT, "include"),
+                    str(src), "-o", str(exe)], check=True, capture_output=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout
+    assert int(out) == L.rsst_config_size()
