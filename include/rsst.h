@@ -50,7 +50,7 @@ extern "C" {
 #define RSST_ECUDA        -2  /* a CUDA runtime/driver call failed */
 #define RSST_ENONPHYSICAL -3  /* rho <= 0, P <= 0 or NaN/Inf produced */
 #define RSST_ETIMEOUT     -4  /* a bounded device wait gave up */
-#define RSST_EUNSUPPORTED -5  /* valid request this build does not provide */
+#define RSST_EUNSUPPORTED -5  /* valid request the library does not provide */
 #define RSST_ENOMEM       -6  /* device allocation failed */
 
 /* Forms of the reduced time derivative (Sec. 3.2 and App. A). */

@@ -69,7 +69,7 @@ void rsst_stage3d_box(int* box_x, int* box_y);  // rsst_fp32_3d.cu
 
 static int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 
-// cuTensorMapEncodeTiled from the driver, looked up once (no link-time libcuda).
+// cuTensorMapEncodeTiled from the CUDA driver, looked up once (no link-time libcuda).
 static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
   if (!fn) {
@@ -89,7 +89,7 @@ static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 // of a tile with its x/y halo for every field.
 static int make_tmap_3d(CUtensorMap* m, void* base, const Geom& g, int nv, int box_x, int box_y) {
   auto enc = tensor_map_encoder();
-  if (!enc) { rsst_set_error("cuTensorMapEncodeTiled unavailable from the driver"); return RSST_ECUDA; }
+  if (!enc) { rsst_set_error("cuTensorMapEncodeTiled unavailable from the CUDA driver"); return RSST_ECUDA; }
   const cuuint64_t dims[4] = {(cuuint64_t)g.pitch, (cuuint64_t)g.py, (cuuint64_t)g.pz, (cuuint64_t)nv};
   const cuuint64_t strides[3] = {(cuuint64_t)g.pitch * 4, (cuuint64_t)g.plane * 4, (cuuint64_t)g.fstride * 4};
   const cuuint32_t box[4] = {(cuuint32_t)box_x, (cuuint32_t)box_y, 1, (cuuint32_t)nv};
@@ -103,7 +103,7 @@ static int make_tmap_3d(CUtensorMap* m, void* base, const Geom& g, int nv, int b
 
 static int make_tmap_2d(CUtensorMap* m, void* base, const Geom& g, int nv, int box_x, int box_y) {
   auto enc = tensor_map_encoder();
-  if (!enc) { rsst_set_error("cuTensorMapEncodeTiled unavailable from the driver"); return RSST_ECUDA; }
+  if (!enc) { rsst_set_error("cuTensorMapEncodeTiled unavailable from the CUDA driver"); return RSST_ECUDA; }
   const cuuint64_t dims[3] = {(cuuint64_t)g.pitch, (cuuint64_t)g.py, (cuuint64_t)nv};
   const cuuint64_t strides[2] = {(cuuint64_t)g.pitch * 4, (cuuint64_t)g.fstride * 4};
   const cuuint32_t box[3] = {(cuuint32_t)box_x, (cuuint32_t)box_y, (cuuint32_t)nv};

@@ -11,7 +11,7 @@ namespace rsst {
 // Equation-of-state hook (Sec. 3.2: the reduced equations hold for a general
 // EOS; the pressure tendency needs (de/dP)_rho and (de/drho)_P, Eqs.
 // pvs_cons_dpr / pvs_cons_therm).  The float64 step reads its thermodynamics
-// only through these members; this build compiles the ideal gas
+// only through these members; the library compiles the ideal gas
 // (e = P/(gamma-1), the only EOS the paper specifies).  Another EOS is a
 // struct with the same members selected by `Eos` below.
 struct IdealGasEos {
