@@ -124,19 +124,24 @@ typedef struct rsst_handle rsst_handle;
  * when a copy, kernel or tensor-map encoding fails.  Synchronous. */
 int rsst_init(rsst_handle** h, const rsst_config* cfg, void* stream);
 
-/* Free everything the handle owns.  Safe on NULL. */
+/* Free everything the handle owns.  Safe on NULL.  Resource management: no
+ * counterpart in the paper. */
 void rsst_destroy(rsst_handle* h);
 
 /* Load the full float64 state (caller layout above) from device memory
  * (on_host = 0) or host memory (on_host = 1), fill the ghost cells, clear
- * the non-physical flag and compute the CFL maximum of the new state.
+ * the non-physical flag and compute the CFL maximum of the new state.  U is
+ * the conserved state (rho, m, E) of Sec. 3.2 that the update of Sec. 4.2
+ * advances, as point values at cell centres.
  * Asynchronous for device input; host input is copied with cudaMemcpyAsync
  * (pinned memory keeps it asynchronous). */
 int rsst_set_state(rsst_handle* h, const double* U, int on_host);
 
 /* Write the full float64 state (background added back in RSST_FP32_PERT
  * mode) to device (on_host = 0) or host (on_host = 1) memory.  Synchronous
- * for host output; returns RSST_ENONPHYSICAL if the flag is set. */
+ * for host output; returns RSST_ENONPHYSICAL if the flag is set (the paper
+ * applies no positivity floors; Sec. 4.2 has no such check, so this flag is
+ * the library's). */
 int rsst_get_state(rsst_handle* h, double* U, int on_host);
 
 /* Advance nsteps SSP-RK2 steps (Sec. 4.2).  dt > 0: fixed step.  dt <= 0:
@@ -157,18 +162,21 @@ int rsst_step(rsst_handle* h, double dt, int nsteps);
 int rsst_set_graph_steps(rsst_handle* h, int32_t k);
 
 /* The step the next adaptive rsst_step will take (cfl / CFL maximum of the
- * current state).  Synchronous. */
+ * current state: the Courant condition of Sec. 4.2).  Synchronous. */
 int rsst_dt(rsst_handle* h, double* dt_out);
 
 /* Simulated time: the sum of the dt of the steps taken since the last
- * rsst_set_state (accumulated on the device).  Synchronous. */
+ * rsst_set_state (accumulated on the device).  Bookkeeping: no counterpart
+ * in the paper.  Synchronous. */
 int rsst_time(rsst_handle* h, double* t);
 
-/* Wait for queued work; RSST_ENONPHYSICAL if a step flagged the state. */
+/* Wait for queued work; RSST_ENONPHYSICAL if a step flagged the state.
+ * Stream control: no counterpart in the paper. */
 int rsst_sync(rsst_handle* h);
 
 /* Sum over cells of each conserved variable times the cell volume, in
- * float64, deterministic order (fixed-shape two-level tree).  In
+ * float64, deterministic order (fixed-shape two-level tree): the totals whose
+ * conservation by form Sec. 5 and App. A discuss.  In
  * RSST_FP32_PERT mode the background's sum (float64) is added to the sum
  * of the perturbation.  `sums` is host memory with nvar entries.
  * Synchronous. */
@@ -182,19 +190,23 @@ int rsst_conserved_sums(rsst_handle* h, double* sums);
  * V = 0).  Gradients are with respect to every component of the initial
  * conserved state and to xi. */
 
-/* Run nsteps fixed-dt steps from the current state, storing a checkpoint of
- * the state every `every` steps.  All device memory the adjoint needs is
+/* Run nsteps fixed-dt steps (Sec. 4.2) from the current state, storing a
+ * checkpoint of the state every `every` steps (checkpointing has no
+ * counterpart in the paper).  All device memory the adjoint needs is
  * allocated here (library-owned): ceil(nsteps/every) checkpoints, 2 x every
  * recompute states and their Euler tendencies, and a few state-sized work
  * arrays; RSST_ENOMEM if that fails.  The handle ends at U^{nsteps}.
  * RSST_EUNSUPPORTED for runs that are not float64.  Asynchronous. */
 int rsst_adjoint_record(rsst_handle* h, double dt, int nsteps, int every);
 
-/* Number of recorded segments, ceil(nsteps / every). */
+/* Number of recorded segments, ceil(nsteps / every) (no counterpart in the
+ * paper).  RSST_EINVAL without a recorded run. */
 int rsst_adjoint_segments(rsst_handle* h, int32_t* nseg);
 
 /* Reverse segment `seg` (call from the last segment down to 0): recompute its
- * steps from the checkpoint, then apply the step adjoints in reverse.  lam:
+ * steps from the checkpoint, then apply the step adjoints in reverse (the
+ * transpose of the Jacobian of the Sec. 4.2 step, a1-a9; no counterpart in
+ * the paper).  lam:
  * device pointer, caller layout, float64; on entry dJ/dU at the segment's end,
  * on return dJ/dU at its start.  *dJ_dxi (host) is incremented by the
  * segment's contribution.  The handle's current state is preserved.
@@ -203,7 +215,8 @@ int rsst_adjoint_step(rsst_handle* h, int32_t seg, double* lam, double* dJ_dxi);
 
 /* J = sum_cells |m|^2/(2 rho) * cell volume of the current state (host
  * double) and, if grad is not NULL, dJ/dU into grad (device, caller layout:
- * (-|V|^2/2, V, 0) * cell volume).  Float64 runs.  Synchronous. */
+ * (-|V|^2/2, V, 0) * cell volume).  The functional of the adjoint
+ * conventions (no counterpart in the paper).  Float64 runs.  Synchronous. */
 int rsst_kinetic_energy(rsst_handle* h, double* J, double* grad);
 
 /* Density gradient at fixed velocity and pressure from a conserved-state
@@ -228,37 +241,55 @@ int rsst_adjoint_rho_fixed_vp(const double* U, const double* lam, double* out, i
  * of a step are captured into a CUDA graph on it). */
 typedef struct rsst_batch rsst_batch;
 
-/* Create nruns runs from cfgs[0..nruns-1] (each as for rsst_init).  Returns
+/* Create nruns runs from cfgs[0..nruns-1] (each as for rsst_init: the
+ * inputs of the scheme of Sec. 4.2 per run).  Returns
  * RSST_EUNSUPPORTED for a run that is not 2D float32-perturbation with a y or
  * no vertical axis.  Synchronous. */
 int rsst_batch_init(rsst_batch** b, int32_t nruns, const rsst_config* cfgs, void* stream);
+
+/* Free every run and the batch's graphs and descriptors.  Safe on NULL.
+ * Resource management: no counterpart in the paper. */
 void rsst_batch_destroy(rsst_batch* b);
 
-/* Per-run state transfer, as rsst_set_state / rsst_get_state. */
+/* Per-run state transfer, as rsst_set_state / rsst_get_state (the state of
+ * Sec. 3.2 per run).  RSST_EINVAL for a run index outside 0..nruns-1. */
 int rsst_batch_set_state(rsst_batch* b, int32_t run, const double* U, int on_host);
+
+/* See rsst_batch_set_state. */
 int rsst_batch_get_state(rsst_batch* b, int32_t run, double* U, int on_host);
 
-/* Advance every run nsteps adaptive SSP-RK2 steps (each with its own CFL dt):
+/* Advance every run nsteps adaptive SSP-RK2 steps of Sec. 4.2 (each with its own CFL dt):
  * per step one graph with two persistent launches over the ragged tile list
  * of all runs.  Asynchronous. */
 int rsst_batch_step(rsst_batch* b, int nsteps);
 
-/* The same steps with one pair of single-run launches per run per step
- * (the reference the persistent kernel is measured against). */
+/* The same steps (Sec. 4.2) with one pair of single-run launches per run per
+ * step (the reference the persistent kernel is measured against). */
 int rsst_batch_step_looped(rsst_batch* b, int nsteps);
 
-/* Each run's next dt (nruns host doubles); wait and report flags.  Synchronous. */
+/* Each run's next dt (nruns host doubles; the Courant condition of Sec. 4.2
+ * per run).  Synchronous. */
 int rsst_batch_dt(rsst_batch* b, double* dts);
+
+/* Wait for every run's queued work; RSST_ENONPHYSICAL if a run's state was
+ * flagged.  Stream control: no counterpart in the paper. */
 int rsst_batch_sync(rsst_batch* b);
 
 /* Time `steps` batch steps for each of six tile shapes (64x32, 32x32, 64x16,
- * 128x16, 64x24, 128x8 cells; index 0..5) on the current states (saved and restored around the
- * trials), keep the fastest; *choice_out gets its index and *ms_out the
- * milliseconds per step (either may be NULL).  With RSST_TUNE_CACHE set to a
- * file name the choice is read from / appended to that file, keyed by the
- * run list.  Synchronous. */
+ * 128x16, 64x24, 128x8 cells; index 0..5) on the current states (saved and
+ * restored around the trials, also after a failed trial), keep the fastest;
+ * *choice_out gets its index and *ms_out the milliseconds per step (either
+ * may be NULL).  With RSST_TUNE_CACHE set to a file name the choice is read
+ * from / appended to that file, keyed by the run list.  A performance
+ * control: no counterpart in the paper.  Synchronous. */
 int rsst_batch_autotune(rsst_batch* b, int steps, int32_t* choice_out, double* ms_out);
+
+/* The tile shape in use, bx x by cells (host outputs).  No counterpart in the
+ * paper.  RSST_EINVAL for NULL arguments. */
 int rsst_batch_tile_shape(const rsst_batch* b, int32_t* bx, int32_t* by);
+
+/* Number of kernels the batch launched so far (0 for NULL).  Bookkeeping:
+ * no counterpart in the paper. */
 int64_t rsst_batch_kernel_launches(const rsst_batch* b);
 
 /* Conservation sums of a caller-held state, for callers that cannot allocate
@@ -282,7 +313,8 @@ int64_t rsst_batch_kernel_launches(const rsst_batch* b);
 int rsst_conserved_sums_noalloc(const double* U, int32_t ndim, const int32_t* n, const double* dx, double* sums,
                                 void* stream);
 
-/* Number of kernels the library launched through this handle so far. */
+/* Number of kernels the library launched through this handle so far (0 for
+ * NULL).  Bookkeeping: no counterpart in the paper. */
 int64_t rsst_kernel_launches(const rsst_handle* h);
 
 /* Self-test of the float64 helpers the kernels use in place of compiler
@@ -299,10 +331,12 @@ int64_t rsst_kernel_launches(const rsst_handle* h);
  * Synchronous, current device. */
 int rsst_math_selftest(int32_t n, double* rcp_max_ulp, int32_t* mc_mismatches, double* sqrt_max_rel);
 
-/* sizeof(rsst_config) as compiled into the library (binding check). */
+/* sizeof(rsst_config) as compiled into the library (binding check; no
+ * counterpart in the paper). */
 size_t rsst_config_size(void);
 
-/* Message describing the calling thread's most recent failure. */
+/* Message describing the calling thread's most recent failure (thread-local
+ * storage owned by the library; no counterpart in the paper). */
 const char* rsst_last_error(void);
 
 #ifdef __cplusplus

@@ -160,3 +160,17 @@ def test_header_is_plain_c_and_matches_the_library(L, tmp_path):
                     str(src), "-o", str(exe)], check=True, capture_output=True)
     out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout
     assert int(out) == L.rsst_config_size()
+
+
+def test_every_entry_point_cites_its_passage_or_says_it_has_none():
+    """Each declaration in include/*.h has its own comment, and that comment
+    cites the paper (Sec., Eq., App.) or states that the paper has no
+    counterpart (or refers to a documented sibling)."""
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        txt = open(h).read()
+        for m in re.finditer(r"^[A-Za-z_][\w\s\*]*?\b(rsst_\w+)\s*\(", txt, flags=re.M):
+            before = txt[:m.start()]
+            end = before.rfind("*/")
+            assert end >= 0 and before[end + 2:].strip() == "", f"{m.group(1)}: no comment of its own"
+            comment = re.sub(r"\s*\n\s*\*?\s*", " ", before[before.rfind("/*", 0, end):end])
+            assert re.search(r"Sec\.|Eq\.|App\.|no counterpart|paper has no|See rsst_", comment, flags=re.I), m.group(1)
