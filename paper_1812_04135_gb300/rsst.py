@@ -285,6 +285,7 @@ class Solver:
 
     def __init__(self, w: dict, precision: str = "fp64", stream=None, **over):
         import torch
+        lib()  # a missing library is reported as such, before the device is touched
         self.w = w
         self.ndim = w["ndim"]
         self.nvar = self.ndim + 2
@@ -405,6 +406,7 @@ class BatchSolver:
 
     def __init__(self, workloads, stream=None):
         import torch
+        lib()  # a missing library is reported as such, before the device is touched
         self.ws = list(workloads)
         self.cfgs = [config_from_workload(w, precision="fp32_pert") for w in self.ws]
         self.stream = stream if stream is not None else torch.cuda.Stream()

@@ -174,3 +174,20 @@ def test_every_entry_point_cites_its_passage_or_says_it_has_none():
             assert end >= 0 and before[end + 2:].strip() == "", f"{m.group(1)}: no comment of its own"
             comment = re.sub(r"\s*\n\s*\*?\s*", " ", before[before.rfind("/*", 0, end):end])
             assert re.search(r"Sec\.|Eq\.|App\.|no counterpart|paper has no|See rsst_", comment, flags=re.I), m.group(1)
+
+
+def test_product_path_fails_loudly_without_the_library(monkeypatch, tmp_path):
+    """No CPU fallback: with the shared library absent, the binding raises
+    before any computation instead of running something else."""
+    monkeypatch.setattr(rsst, "LIB_PATH", str(tmp_path / "absent" / "librsst.so"))
+    monkeypatch.setattr(rsst, "_lib", None)
+    with pytest.raises(ImportError):
+        rsst.lib()
+    from paper_1812_04135_gb300 import inputs
+    w = inputs.random_smooth_state(1, (8,), xi=2.0)
+    with pytest.raises(ImportError):
+        rsst.Solver(w, "fp64")
+    with pytest.raises(ImportError):
+        rsst.BatchSolver([inputs.shear_layer_2d(8, 8)])
+    with pytest.raises(ImportError):
+        rsst.rsst_init(rsst.config_from_workload(w), stream=0)
