@@ -34,6 +34,11 @@
  *  - A non-physical state (rho <= 0, P <= 0 or a non-finite value) found
  *    by a step sets a sticky device flag; the next synchronous call returns
  *    RSST_ENONPHYSICAL.  The output is still written.  No floors are applied.
+ *  - Every device wait of the TMA-staged kernels is bounded (2 s).  A wait
+ *    that runs out sets a second flag bit: the kernel waits (bounded) for
+ *    the copies it issued and returns, and the next synchronous call returns
+ *    RSST_ETIMEOUT (reported before RSST_ENONPHYSICAL).  The context stays
+ *    usable; rsst_set_state clears both bits.
  */
 #ifndef RSST_H
 #define RSST_H
@@ -174,6 +179,19 @@ int rsst_time(rsst_handle* h, double* t);
  * Stream control: no counterpart in the paper. */
 int rsst_sync(rsst_handle* h);
 
+/* Failure-detection test hook (no counterpart in the paper).  With
+ * limit_ns > 0, from the next step on every tile of the 2D
+ * RSST_FP32_PERT TMA stage kernel, once its own copy has landed (so no copy
+ * is in flight), also waits up to limit_ns on a shared-memory barrier that
+ * nothing completes.  The wait runs out, the kernel sets the run's timeout
+ * flag and returns without writing that tile, and the next synchronous call
+ * returns RSST_ETIMEOUT; the state is then incomplete (load one with
+ * rsst_set_state).  limit_ns = 0 restores normal steps.  Errors: RSST_EINVAL
+ * unless 0 <= limit_ns <= 1e9; RSST_EUNSUPPORTED for runs that do not use
+ * that kernel (it serves 2D RSST_FP32_PERT runs with vertical axis y or
+ * none).  Synchronous, launches nothing. */
+int rsst_debug_stall_wait(rsst_handle* h, int64_t limit_ns);
+
 /* Sum over cells of each conserved variable times the cell volume, in
  * float64, deterministic order (fixed-shape two-level tree): the totals whose
  * conservation by form Sec. 5 and App. A discuss.  In
@@ -271,9 +289,19 @@ int rsst_batch_step_looped(rsst_batch* b, int nsteps);
  * per run).  Synchronous. */
 int rsst_batch_dt(rsst_batch* b, double* dts);
 
-/* Wait for every run's queued work; RSST_ENONPHYSICAL if a run's state was
- * flagged.  Stream control: no counterpart in the paper. */
+/* Wait for every run's queued work and check every run's flag:
+ * RSST_ETIMEOUT if a bounded device wait gave up in any run (the message
+ * names the first such run and the count; a persistent block that gives up
+ * flags every run whose tiles it leaves unwritten), else RSST_ENONPHYSICAL
+ * if a run's state was flagged.  Stream control: no counterpart in the
+ * paper. */
 int rsst_batch_sync(rsst_batch* b);
+
+/* rsst_debug_stall_wait for run `run` of a batch, in the persistent kernel
+ * (no counterpart in the paper).  Waits for the batch's stream, then
+ * rebuilds the run descriptors with the setting (graphs are recaptured on
+ * the next step).  RSST_EINVAL for a bad run index or limit. */
+int rsst_batch_debug_stall_wait(rsst_batch* b, int32_t run, int64_t limit_ns);
 
 /* Time `steps` batch steps for each of six tile shapes (64x32, 32x32, 64x16,
  * 128x16, 64x24, 128x8 cells; index 0..5) on the current states (saved and

@@ -329,12 +329,23 @@ fail:
   return rc;
 }
 
-static int check_flag(rsst_handle* h) {
+int rsst_read_flag(rsst_handle* h, unsigned int* flag) {
   CUDA_TRY(cudaMemcpyAsync(h->h_small, h->d_flag, sizeof(unsigned int), cudaMemcpyDeviceToHost, h->stream));
   CUDA_TRY(cudaStreamSynchronize(h->stream));
-  unsigned int f;
-  memcpy(&f, h->h_small, sizeof f);
-  if (f) {
+  memcpy(flag, h->h_small, sizeof *flag);
+  return RSST_OK;
+}
+
+// A timeout is reported first: a stage that gave up left part of its output
+// unwritten, which may also look non-physical.
+static int check_flag(rsst_handle* h) {
+  unsigned int f = 0;
+  RC_TRY(rsst_read_flag(h, &f));
+  if (f & RSST_FLAG_TIMEOUT) {
+    rsst_set_error("a bounded device wait (TMA copy or barrier) gave up: the step's output is incomplete");
+    return RSST_ETIMEOUT;
+  }
+  if (f & RSST_FLAG_NONPHYSICAL) {
     rsst_set_error("non-physical state (rho <= 0, P <= 0 or NaN) produced");
     return RSST_ENONPHYSICAL;
   }
@@ -404,6 +415,7 @@ static int plain_steps(rsst_handle* h, double dt, int nsteps, cudaStream_t st) {
   a.scal = h->d_scal;
   a.flag = h->d_flag;
   a.dt_fixed = dt > 0.0 ? dt : 0.0;
+  a.stall_ns = h->stall_ns;
   T* U = (T*)h->buf[0];
   T* Us = (T*)h->buf[1];
   for (int s = 0; s < nsteps; ++s) {
@@ -510,6 +522,20 @@ extern "C" int rsst_set_graph_steps(rsst_handle* h, int32_t k) {
   }
   if (k != h->graph_steps) drop_graphs(h);
   h->graph_steps = k;
+  return RSST_OK;
+}
+
+extern "C" int rsst_debug_stall_wait(rsst_handle* h, int64_t limit_ns) {
+  if (!h || limit_ns < 0 || limit_ns > 1000000000LL) {
+    rsst_set_error("rsst_debug_stall_wait: need a handle and 0 <= limit_ns <= 1e9");
+    return RSST_EINVAL;
+  }
+  if (!h->use_tma2d) {
+    rsst_set_error("rsst_debug_stall_wait: only runs on the 2D float32-perturbation TMA kernel have the test wait");
+    return RSST_EUNSUPPORTED;
+  }
+  if (limit_ns != h->stall_ns) drop_graphs(h);  // graphs hold the stage arguments by value
+  h->stall_ns = limit_ns;
   return RSST_OK;
 }
 

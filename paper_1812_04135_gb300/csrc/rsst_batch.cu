@@ -8,7 +8,7 @@
 // the single-run kernel with that run's tensor map, tables, dt and CFL slot.
 // The two stages of one step are captured once per CFL-slot parity into a
 // CUDA graph and replayed.  The tile shape is chosen by a timing autotuner
-// over four candidates (optionally cached in the file named by
+// over six candidates (optionally cached in the file named by
 // RSST_TUNE_CACHE).
 #include <cstdio>
 #include <cstdlib>
@@ -78,9 +78,25 @@ __global__ void __launch_bounds__(C::NT) batch_stage_kernel(const BatchRun* __re
     bool ok = true;
     const bool fine = br.vert == 1 ? tile2d_f<C, 1>(map, *sr, *sdt, tx, ty, smem_raw, phase, rmax, ok)
                                    : tile2d_f<C, -1>(map, *sr, *sdt, tx, ty, smem_raw, phase, rmax, ok);
-    if (!fine) return;
+    if (!fine) {
+      // A bounded wait gave up (the tile routine has already waited for its
+      // copy).  This block leaves the rest of the stage: every run that owns
+      // one of its remaining tiles gets the timeout flag, so no run is left
+      // partly unwritten without being reported.
+      if (threadIdx.x == 0) {
+        for (int u = t + gridDim.x; u < total_tiles; u += gridDim.x) {
+          int lo = 0, hi = nruns - 1;
+          while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (tile_begin[mid] <= u) lo = mid; else hi = mid - 1;
+          }
+          atomicOr(runs[lo].r.flag, RSST_FLAG_TIMEOUT);
+        }
+      }
+      return;
+    }
     if (stage == 2) {
-      if (!ok) atomicOr(sr->flag, 1u);
+      if (!ok) atomicOr(sr->flag, RSST_FLAG_NONPHYSICAL);
       block_max_to<C::NT>((double)rmax, br.scal + (slot ^ 1), t2_sred<C>(smem_raw));
     }
     __syncthreads();  // the descriptor copy is rewritten for the next tile
@@ -181,6 +197,7 @@ static int build_descriptors(rsst_batch* b, int c) {
     br.r.tab = h->d_tab;
     br.r.tab_len = h->bg_len;
     br.r.flag = h->d_flag;
+    br.r.stall_ns = h->stall_ns;
     br.scal = h->d_scal;
     br.tiles_x = (h->g.n[0] + bx - 1) / bx;
     br.vert = h->d_tab ? 1 : -1;
@@ -373,11 +390,44 @@ extern "C" int rsst_batch_dt(rsst_batch* b, double* dts) {
 
 extern "C" int rsst_batch_sync(rsst_batch* b) {
   if (!b) { rsst_set_error("NULL batch"); return RSST_EINVAL; }
-  for (rsst_handle* h : b->runs) {
-    const int rc = rsst_sync(h);
+  // Every run is checked; a timeout is reported before a non-physical state
+  // (a run whose stage gave up may hold a partly written state).
+  int worst = RSST_OK, first_timeout = -1, first_bad = -1, ntimeout = 0, nbad = 0;
+  for (int i = 0; i < b->nruns; ++i) {
+    unsigned int f = 0;
+    const int rc = rsst_read_flag(b->runs[i], &f);
     if (rc != RSST_OK) return rc;
+    if (f & RSST_FLAG_TIMEOUT) {
+      if (first_timeout < 0) first_timeout = i;
+      ++ntimeout;
+    } else if (f & RSST_FLAG_NONPHYSICAL) {
+      if (first_bad < 0) first_bad = i;
+      ++nbad;
+    }
   }
-  return RSST_OK;
+  if (ntimeout) {
+    rsst_set_error("a bounded device wait gave up in %d run(s), first run %d: their states are incomplete",
+                   ntimeout, first_timeout);
+    worst = RSST_ETIMEOUT;
+  } else if (nbad) {
+    rsst_set_error("non-physical state (rho <= 0, P <= 0 or NaN) produced in %d run(s), first run %d", nbad,
+                   first_bad);
+    worst = RSST_ENONPHYSICAL;
+  }
+  return worst;
+}
+
+extern "C" int rsst_batch_debug_stall_wait(rsst_batch* b, int32_t run, int64_t limit_ns) {
+  if (!b || run < 0 || run >= b->nruns || limit_ns < 0 || limit_ns > 1000000000LL) {
+    rsst_set_error("rsst_batch_debug_stall_wait: need a batch, a run index and 0 <= limit_ns <= 1e9");
+    return RSST_EINVAL;
+  }
+  if (cudaStreamSynchronize(b->stream) != cudaSuccess) {  // no step may read the descriptors meanwhile
+    rsst_set_error("rsst_batch_debug_stall_wait: %s", cudaGetErrorString(cudaGetLastError()));
+    return RSST_ECUDA;
+  }
+  b->runs[run]->stall_ns = limit_ns;
+  return build_descriptors(b, b->choice);  // the descriptors carry the setting; graphs are recaptured
 }
 
 extern "C" int rsst_batch_tile_shape(const rsst_batch* b, int32_t* bx, int32_t* by) {

@@ -280,7 +280,7 @@ __global__ void __launch_bounds__(NT) stage_df_kernel(const DFArgs a) {
     store_ghosts_df<NV>(a.out, g, a.p, a.bg, a.bg_len, i, j, k, u);
   }
   if (a.stage == 2) {
-    if (!ok_all) atomicOr(a.flag, 1u);
+    if (!ok_all) atomicOr(a.flag, RSST_FLAG_NONPHYSICAL);
     block_max_df<NT>(rmax, a.scal + (a.slot ^ 1), sred);
   }
 }
@@ -359,7 +359,7 @@ __global__ void __launch_bounds__(256) cfl_df_kernel(const float2* __restrict__ 
     if (ok && df_lt(rmax, r)) rmax = r;
     ok_all = ok_all && ok;
   }
-  if (!ok_all) atomicOr(flag, 1u);
+  if (!ok_all) atomicOr(flag, RSST_FLAG_NONPHYSICAL);
   block_max_df<256>(rmax, dst, sred);
 }
 

@@ -395,7 +395,7 @@ __global__ void __launch_bounds__(NT) stage_fp32_kernel(const StageArgs<float> a
     store_mirror_ghosts<float, NV>(a.out, g, p, i, j, k, u);
   }
   if (a.stage == 2) {
-    if (!ok_all) atomicOr(a.flag, 1u);
+    if (!ok_all) atomicOr(a.flag, RSST_FLAG_NONPHYSICAL);
     block_max_to<NT>((double)rmax, a.scal + (a.slot ^ 1), sred);
   }
 }
@@ -504,7 +504,7 @@ __global__ void __launch_bounds__(256) cfl_fp32_kernel(const float* __restrict__
     if (ok) rmax = fmaxf(rmax, (sqrtf(w2) + sound_over_xi_f(pf.gamma * Pn * irn, pf)) * pf.sum_inv_dx);
     ok_all = ok_all && ok;
   }
-  if (!ok_all) atomicOr(flag, 1u);
+  if (!ok_all) atomicOr(flag, RSST_FLAG_NONPHYSICAL);
   block_max_to<256>((double)rmax, dst, sred);
 }
 

@@ -34,6 +34,7 @@ __global__ void __launch_bounds__(T2::NT, 5) stage2d_tma_kernel(const __grid_con
   r.tab_len = a.tab_len;
   r.flag = a.flag;
   r.stage = a.stage;
+  r.stall_ns = a.stall_ns;
   uint64_t* bar = t2_barrier<T2>(smem_raw);
   float* sdt = reinterpret_cast<float*>(bar + 1);
   if (threadIdx.x == 0) {
@@ -56,7 +57,7 @@ __global__ void __launch_bounds__(T2::NT, 5) stage2d_tma_kernel(const __grid_con
   const bool fine = tile2d_f<T2, VERT>(&tin, r, dtf, blockIdx.x, blockIdx.y, smem_raw, phase, rmax, ok);
   if (!fine) return;
   if (a.stage == 2) {
-    if (!ok) atomicOr(a.flag, 1u);
+    if (!ok) atomicOr(a.flag, RSST_FLAG_NONPHYSICAL);
     block_max_to<T2::NT>((double)rmax, a.scal + (a.slot ^ 1), t2_sred<T2>(smem_raw));
   }
 }

@@ -26,6 +26,7 @@ struct T2Cfg {
   static constexpr uint32_t BOX_BYTES = U_FLOATS * 4;
   static constexpr size_t smem_bytes() { return SCRATCH + 16 + 8 * 8 + 512 + 128; }
   static_assert(BY % SEG == 0, "column segments must tile BY");
+  static_assert(SCRATCH % 8 == 0, "the barriers after the scratch area need 8-byte alignment");
   static_assert(SXP <= 256 && SYP <= 256, "TMA box dimensions are at most 256");
 };
 
@@ -44,6 +45,11 @@ template <class C>
 __device__ __forceinline__ unsigned char* t2_extra(unsigned char* smem) {
   return smem + C::SCRATCH + 16 + 8 * 8;
 }
+// barrier of the failure-detection test wait (after the batched kernel's 512 bytes)
+template <class C>
+__device__ __forceinline__ uint64_t* t2_stall_barrier(unsigned char* smem) {
+  return reinterpret_cast<uint64_t*>(smem + C::SCRATCH + 16 + 8 * 8 + 512);
+}
 
 // Everything one tile needs about its run.
 struct TileRun {
@@ -56,6 +62,7 @@ struct TileRun {
   int tab_len;
   unsigned int* flag;
   int stage;
+  int64_t stall_ns;  // > 0 only in failure-detection tests (see tile2d_f)
 };
 
 // LLF flux of the x face between tile cells with smem columns c-1 | c (row sr).
@@ -174,6 +181,22 @@ __device__ __forceinline__ bool tile2d_f(const CUtensorMap* tin, const TileRun& 
     return false;
   }
   phase ^= 1u;
+  if (r.stall_ns > 0) {
+    // Failure-detection test: with the tile's copy landed (nothing in
+    // flight), wait on a barrier that expects 16 bytes no copy delivers, so
+    // the bounded wait runs out and the give-up path above is taken.
+    uint64_t* sb = t2_stall_barrier<T2>(smem);
+    if (tid == 0) {
+      mbar_init(sb, 1);
+      fence_mbar_init();
+      mbar_expect_tx(sb, 16);
+    }
+    __syncthreads();
+    if (__syncthreads_or(!mbar_wait_bounded(sb, 0u, (uint64_t)r.stall_ns))) {
+      if (tid == 0) atomicOr(r.flag, RSST_FLAG_TIMEOUT);
+      return false;
+    }
+  }
 
   // x faces
   const int nx = g.n[0], ny = g.n[1];

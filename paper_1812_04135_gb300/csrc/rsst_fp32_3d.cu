@@ -161,9 +161,10 @@ __global__ void __launch_bounds__(T3::NT, 2) stage3d_tma_kernel(const __grid_con
     mbar_expect_tx(&bar[s], T3::BOX_BYTES);
     tma_load_4d(ring + s * T3::PLANE, &tin, &bar[s], i0 + g.xoff - T3::XO, j0, pl + RSST_G, 0);
   };
+  int issued = min(pfirst + 4, plast);  // last plane whose copy has been issued
   if (tid == 0) {
     fence_proxy_async_smem();
-    for (int pl = pfirst; pl <= min(pfirst + 4, plast); ++pl) issue(pl);
+    for (int pl = pfirst; pl <= issued; ++pl) issue(pl);
   }
   if constexpr (VERT >= 0) {
     for (int id = tid; id < T3::TAB_FLOATS; id += T3::NT) {
@@ -181,10 +182,19 @@ __global__ void __launch_bounds__(T3::NT, 2) stage3d_tma_kernel(const __grid_con
     if (pl > waited) waited = pl;
     return true;
   };
+  // Giving up: flag the run, and before the CTA leaves, wait (bounded) for
+  // every plane copy still in flight, so that none lands in shared memory
+  // the next CTA on this SM may own.
+  auto give_up = [&]() {
+    if (tid == 0) {
+      atomicOr(a.flag, RSST_FLAG_TIMEOUT);
+      for (int q = waited + 1; q <= issued; ++q) mbar_wait_bounded(&bar[slot_of(q)], phase_of(q));
+    }
+  };
   // the give-up decision is taken by the whole block (no thread may leave
   // while others wait at a barrier)
   if (__syncthreads_or(!wait_upto(pfirst + 3))) {
-    if (tid == 0) atomicOr(a.flag, RSST_FLAG_TIMEOUT);
+    give_up();
     return;
   }
 
@@ -217,12 +227,15 @@ __global__ void __launch_bounds__(T3::NT, 2) stage3d_tma_kernel(const __grid_con
   for (int k = k0; k < k1; ++k) {
     // everyone sees plane k+2 and the slot of plane k-3 is free
     if (__syncthreads_or(!wait_upto(k + 2))) {
-      if (tid == 0) atomicOr(a.flag, RSST_FLAG_TIMEOUT);
+      give_up();
       return;
     }
-    if (tid == 0 && k + 3 <= plast) {
-      fence_proxy_async_smem();
-      issue(k + 3);
+    if (k + 3 <= plast) {
+      if (tid == 0) {
+        fence_proxy_async_smem();
+        issue(k + 3);
+      }
+      issued = k + 3;
     }
     const int rz = k - k0 + 2;  // table row of plane k
     float rho0 = 0.0f, P0 = 0.0f, H0 = 0.0f;
@@ -294,7 +307,7 @@ __global__ void __launch_bounds__(T3::NT, 2) stage3d_tma_kernel(const __grid_con
     }
   }
   if (a.stage == 2) {
-    if (!ok_all) atomicOr(a.flag, 1u);
+    if (!ok_all) atomicOr(a.flag, RSST_FLAG_NONPHYSICAL);
     block_max_to<T3::NT>((double)rmax, a.scal + (a.slot ^ 1), sred);
   }
 }

@@ -267,7 +267,7 @@ __global__ void __launch_bounds__(NT, NDIM == 3 ? 3 : 0) stage_fp64_kernel(const
     store_with_ghosts<NV>(a.out, g, p, a.bg, a.bg_len, i, j, k, u);
   }
   if (a.stage == 2) {
-    if (!ok_all) atomicOr(a.flag, 1u);
+    if (!ok_all) atomicOr(a.flag, RSST_FLAG_NONPHYSICAL);
     block_max_to<NT>(rmax, a.scal + (a.slot ^ 1), sred);
   }
 }
@@ -350,7 +350,7 @@ __global__ void __launch_bounds__(256) cfl_fp64_kernel(const double* __restrict_
     if (ok) rmax = fmax(rmax, r);
     ok_all = ok_all && ok;
   }
-  if (!ok_all) atomicOr(flag, 1u);
+  if (!ok_all) atomicOr(flag, RSST_FLAG_NONPHYSICAL);
   block_max_to<256>(rmax, dst, sred);
 }
 

@@ -13,6 +13,10 @@
 // thread), so that a short line runs on many SMs instead of one CTA on one SM
 #define RSST_SMALL_1D (32 * 152 * 4)
 
+// Bits of a run's device flag (sticky until the next rsst_set_state).
+#define RSST_FLAG_NONPHYSICAL 1u  // a stage produced rho <= 0, P <= 0 or a non-finite value
+#define RSST_FLAG_TIMEOUT 2u      // a bounded wait on a TMA copy or barrier gave up
+
 // Padded device layout of one run's state, per field:
 //   interior cell (i, j, k) lives at  (k + gz) * plane + (j + gy) * pitch + (i + xoff)
 // with two ghost cells before and after the interior on every active axis.
@@ -96,6 +100,8 @@ struct StageArgs {
   int tab_len;
   double* dU_out;   // float64 kernels: if set, the Euler tendency of each interior cell
                     // (padded layout) is written here too (adjoint recompute)
+  int64_t stall_ns; // > 0 (failure-detection tests only): each tile of the 2D TMA kernel
+                    // also waits this long on a barrier that nothing completes
 };
 
 // Host-side launchers (defined in the .cu files).
@@ -163,9 +169,12 @@ struct rsst_handle {
   int gvalid[2];
   double gdt[2];            // the dt each graph was captured with
   double* rec_dU[2];        // float64 plain steps: Euler tendency of stage 1 / 2 written here if set
+  int64_t stall_ns;         // rsst_debug_stall_wait (0: normal steps)
 };
 
 void rsst_adjoint_free(rsst_handle* h);
 
 // Step a single run (used by rsst_step and by the batch's looped mode).
 int rsst_handle_steps(rsst_handle* h, double dt, int nsteps);
+// Wait for the run's queued work and read its device flag (RSST_FLAG_* bits).
+int rsst_read_flag(rsst_handle* h, unsigned int* flag);

@@ -1,15 +1,17 @@
 // TMA (cp.async.bulk.tensor) and mbarrier helpers, inline PTX for sm_103a.
 //
 // Every wait is bounded by the global timer: a copy that has not completed
-// after RSST_WAIT_NS sets an error bit in the caller's flag and the kernel
-// returns instead of spinning forever.
+// after RSST_WAIT_NS sets RSST_FLAG_TIMEOUT in the run's flag and the kernel
+// returns (after a bounded wait for the copies it has issued) instead of
+// spinning forever.
 #pragma once
 
 #include <cuda.h>
 #include <stdint.h>
 
+#include "rsst_internal.h"
+
 #define RSST_WAIT_NS 2000000000ull  // 2 s
-#define RSST_FLAG_TIMEOUT 2u
 
 namespace rsst {
 
@@ -45,12 +47,12 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t phase) {
   return ok != 0;
 }
 
-// Wait for the phase with parity `phase` to complete; false after RSST_WAIT_NS.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t phase) {
+// Wait for the phase with parity `phase` to complete; false after limit_ns.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t phase, uint64_t limit_ns = RSST_WAIT_NS) {
   if (mbar_try_wait(bar, phase)) return true;
   const uint64_t t0 = global_ns();
   while (!mbar_try_wait(bar, phase)) {
-    if (global_ns() - t0 > RSST_WAIT_NS) return false;
+    if (global_ns() - t0 > limit_ns) return false;
   }
   return true;
 }

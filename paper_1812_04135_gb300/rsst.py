@@ -59,6 +59,8 @@ def lib():
             "rsst_set_graph_steps": (i32, [vp, i32]),
             "rsst_dt": (i32, [vp, pd]),
             "rsst_sync": (i32, [vp]),
+            "rsst_debug_stall_wait": (i32, [vp, i64]),
+            "rsst_batch_debug_stall_wait": (i32, [vp, i32, i64]),
             "rsst_time": (i32, [vp, pd]),
             "rsst_conserved_sums": (i32, [vp, pd]),
             "rsst_kernel_launches": (i64, [vp]),
@@ -206,6 +208,12 @@ def rsst_time(h: int) -> float:
 
 def rsst_sync(h: int) -> None:
     _check(lib().rsst_sync(h), "rsst_sync")
+
+
+def rsst_debug_stall_wait(h: int, limit_ns: int) -> None:
+    """Failure-detection test hook: each tile of the 2D float32 TMA kernel
+    also waits limit_ns on a barrier nothing completes (0: off)."""
+    _check(lib().rsst_debug_stall_wait(h, int(limit_ns)), "rsst_debug_stall_wait")
 
 
 def rsst_conserved_sums(h: int, nvar: int) -> list:
@@ -382,6 +390,10 @@ def rsst_batch_dt(b: int, nruns: int) -> list:
 
 def rsst_batch_sync(b: int) -> None:
     _check(lib().rsst_batch_sync(b), "rsst_batch_sync")
+
+
+def rsst_batch_debug_stall_wait(b: int, run: int, limit_ns: int) -> None:
+    _check(lib().rsst_batch_debug_stall_wait(b, int(run), int(limit_ns)), "rsst_batch_debug_stall_wait")
 
 
 def rsst_batch_autotune(b: int, steps: int = 3):
