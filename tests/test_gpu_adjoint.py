@@ -89,6 +89,24 @@ def test_kinetic_energy_and_gradient():
     assert close(g.cpu(), ro.kinetic_energy_gradient(U, prob), 1e-14)
 
 
+@pytest.mark.parametrize("ndim,n,dx", [(1, (40,), (0.3,)), (2, (30, 20), (0.1, 0.4)), (3, (12, 10, 9), (0.2, 0.5, 0.125))])
+def test_kinetic_energy_of_a_uniform_moving_gas(ndim, n, dx):
+    """The device functional against its closed form, 1/2 rho |V|^2 times the
+    domain volume, for a gas moving uniformly (no oracle involved)."""
+    rho, V, E = 2.5, (0.3, -0.7, 1.1)[:ndim], 9.0
+    w = inputs.random_smooth_state(ndim, n, xi=3.0)
+    shape = tuple(reversed(n))
+    w["U"] = np.ascontiguousarray(np.stack([np.full(shape, rho)] + [np.full(shape, rho * V[d]) for d in range(ndim)]
+                                           + [np.full(shape, E)]))
+    w["dx"] = tuple(dx)
+    volume = float(np.prod([n[d] * dx[d] for d in range(ndim)]))
+    s = rsst.Solver(w, "fp64")
+    s.set_state(torch.from_numpy(w["U"]).cuda())
+    J = rsst.rsst_kinetic_energy(s.h)
+    s.close()
+    assert J == pytest.approx(0.5 * rho * sum(v * v for v in V) * volume, rel=1e-13)
+
+
 def test_autograd_function():
     w = inputs.polytrope_2d(16, 24, xi=20.0, contrast=20.0, amp=1e-2)
     prob, U = problem_from(w)

@@ -9,7 +9,7 @@ import torch
 from oracle import rsst_oracle as ro
 from oracle.workload import problem_from
 from paper_1812_04135_gb300 import inputs, rsst
-from tests.parity import rel_linf
+from tests.parity import check_precision, rel_linf
 
 pytestmark = pytest.mark.gpu
 TOL = {"fp64": 1e-10, "fp64_df": 1e-10, "fp32_pert": 1e-5}
@@ -49,8 +49,7 @@ def test_min_width_cfl_rule_matches_oracle(name, precision):
     s.step(5)
     got = s.get_state("cpu")
     s.close()
-    err = rel_linf(got, ref, w["gamma"])
-    assert max(err) < TOL[precision], (name, precision, err)
+    check_precision(got, ref, w, U, prob, 5, precision, TOL[precision], what=name)
 
 
 def test_min_width_cfl_rule_in_the_batched_kernel():

@@ -6,7 +6,7 @@ import torch
 from oracle import rsst_oracle as ro
 from oracle.workload import problem_from
 from paper_1812_04135_gb300 import inputs, rsst
-from tests.parity import rel_linf
+from tests.parity import assert_parity
 
 pytestmark = pytest.mark.gpu
 TOL = 1e-10
@@ -38,8 +38,11 @@ def ref(w, nsteps, dt=None):
 
 
 def check(w, nsteps, tol=TOL, what=""):
-    err = rel_linf(run(w, nsteps), ref(w, nsteps), w["gamma"])
-    assert max(err) < tol, (what, err)
+    """Own-scale parity at 1e-10, or within the oracle's round-off floor for
+    the double-float unit round-off 2^-48 (tests/parity.py)."""
+    prob, U = problem_from(w)
+    assert_parity(run(w, nsteps), ro.run(U, prob, nsteps), w, U, prob, nsteps, precision="fp64_df", tol=tol,
+                  what=what)
 
 
 @pytest.mark.parametrize("ndim", [1, 2, 3])

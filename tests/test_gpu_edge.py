@@ -10,7 +10,7 @@ import torch
 from oracle import rsst_oracle as ro
 from oracle.workload import problem_from
 from paper_1812_04135_gb300 import inputs, rsst
-from tests.parity import rel_linf
+from tests.parity import check_precision, rel_linf
 
 pytestmark = pytest.mark.gpu
 TOL = {"fp64": 1e-10, "fp64_df": 1e-10, "fp32_pert": 1e-5}
@@ -45,8 +45,7 @@ def test_smallest_grids(precision, n, bc):
     w = inputs.random_smooth_state(len(n), n, xi=4.0, variant="pvs", bc=bc)
     prob, U = problem_from(w)
     ref = ro.run(U, prob, 3)
-    err = rel_linf(gpu_run(w, precision, 3), ref, w["gamma"])
-    assert max(err) < TOL[precision], (precision, n, bc, err)
+    check_precision(gpu_run(w, precision, 3), ref, w, U, prob, 3, precision, TOL[precision], what=(n, bc))
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp64_df", "fp32_pert"])

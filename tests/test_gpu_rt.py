@@ -13,7 +13,7 @@ import torch
 from oracle import rsst_oracle as ro
 from oracle.workload import problem_from
 from paper_1812_04135_gb300 import inputs, rsst
-from tests.parity import rel_linf
+from tests.parity import check_precision
 
 pytestmark = pytest.mark.gpu
 
@@ -37,7 +37,7 @@ def test_rt_matches_oracle(precision, tol):
     s.close()
     prob, U = problem_from(w)
     ref = ro.run(U, prob, 5)
-    assert max(rel_linf(got, ref, w["gamma"])) < tol
+    check_precision(got, ref, w, U, prob, 5, precision, tol)
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32_pert"])

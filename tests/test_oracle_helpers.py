@@ -1,7 +1,8 @@
 """Pins of the oracle's helpers that the step-level pins reach only
 indirectly: the ghost cells of each boundary (reading 7), the consistency of
 the face fluxes (Sec. 4.2: the LLF flux of a uniform state is its Euler
-flux), the kinetic-energy functional's gradient the adjoint starts from, and
+flux), the kinetic-energy functional the adjoint differentiates (closed-form
+values) and its gradient, and
 the non-physical check (reading 9).  Expected values are written out index by
 index in Python, not with the tensor operations the oracle uses."""
 import math
@@ -117,6 +118,40 @@ def test_kinetic_energy_gradient_matches_central_differences():
                 Um[v, j, i] -= h
                 fd = (float(ro.kinetic_energy(Up, prob)) - float(ro.kinetic_energy(Um, prob))) / (2 * h)
                 assert G[v, j, i] == pytest.approx(fd, rel=1e-7, abs=1e-10)
+
+
+def _moving_gas(ndim, n, rho, V, E):
+    shape = tuple(reversed(n))
+    return torch.stack([torch.full(shape, rho, dtype=DT)] + [torch.full(shape, rho * V[d], dtype=DT)
+                                                              for d in range(ndim)] + [torch.full(shape, E, dtype=DT)])
+
+
+@pytest.mark.parametrize("ndim,n,dx", [(1, (10,), (0.3,)), (2, (6, 5), (0.1, 0.4)),
+                                       (3, (4, 3, 5), (0.2, 0.5, 0.125))])
+def test_kinetic_energy_of_a_uniform_moving_gas(ndim, n, dx):
+    """J of a gas moving uniformly is 1/2 rho |V|^2 times the domain volume
+    (n_d dx_d along every axis): a dropped 1/2, a missing cell width, or m^2
+    instead of m^2/rho (rho != 1 here) changes it."""
+    rho, V = 2.5, (0.3, -0.7, 1.1)[:ndim]
+    prob = ro.Problem(ndim=ndim, n=n, dx=dx, gamma=1.4)
+    volume = 1.0
+    for d in range(ndim):
+        volume *= n[d] * dx[d]
+    want = 0.5 * rho * sum(v * v for v in V) * volume
+    assert float(ro.kinetic_energy(_moving_gas(ndim, n, rho, V, 9.0), prob)) == pytest.approx(want, rel=1e-14)
+
+
+def test_kinetic_energy_of_a_sine_velocity():
+    """V_x = sin(2 pi x_i) at the N cell centres of [0, 1), rho = 3: the sum of
+    sin^2 over a full period of N >= 3 points is N/2, so J = 1/2 rho (1/2) L
+    with L = N dx = 1."""
+    N = 16
+    x = (torch.arange(N, dtype=DT) + 0.5) / N
+    rho = 3.0
+    v = torch.sin(2 * math.pi * x)
+    U = torch.stack([torch.full((N,), rho, dtype=DT), rho * v, torch.full((N,), 10.0, dtype=DT)])
+    prob = ro.Problem(ndim=1, n=(N,), dx=(1.0 / N,), gamma=1.4)
+    assert float(ro.kinetic_energy(U, prob)) == pytest.approx(0.5 * rho * 0.5, rel=1e-14)
 
 
 @pytest.mark.parametrize("field,value", [(0, 0.0), (0, -1.0), (3, 0.1), (1, float("nan")), (3, float("inf"))])
