@@ -179,6 +179,9 @@ static void make_physf(const Phys* p, PhysF* f) {
     f->inv_dx[d] = (float)p->inv_dx[d];
   }
   f->sum_inv_dx = (float)p->sum_inv_dx;
+  f->hgm1 = (float)p->hgm1;
+  f->gam_gm1 = (float)(p->gamma / p->gm1);
+  f->gx = (float)(p->use_cmax ? p->gamma : p->gamma_xi2);
 }
 
 static void make_phys(const rsst_config* c, Phys* p) {
@@ -234,6 +237,7 @@ extern "C" void rsst_destroy(rsst_handle* h) {
   cudaFree(h->d_partial);
   cudaFree(h->d_stage);
   cudaFree(h->d_tab);
+  cudaFree(h->d_tabr);
   cudaFreeHost(h->h_small);
   delete h;
 }
@@ -292,7 +296,8 @@ extern "C" int rsst_init(rsst_handle** out, const rsst_config* cfg, void* stream
     if (e != cudaSuccess) { rsst_set_error("background upload: %s", cudaGetErrorString(e)); rc = RSST_ECUDA; goto fail; }
     if (cfg->precision == RSST_FP32_PERT) {
       ALLOC(h->d_tab, (size_t)TB_COUNT * h->bg_len * sizeof(float));
-      rc = rsst_launch_bgtab(h->d_bg, h->bg_len, h->g, h->p, h->d_tab, 0);
+      ALLOC(h->d_tabr, (size_t)TR_W * h->bg_len * sizeof(float));
+      rc = rsst_launch_bgtab(h->d_bg, h->bg_len, h->g, h->p, h->d_tab, h->d_tabr, 0);
       if (rc != RSST_OK) goto fail;
       if (cudaDeviceSynchronize() != cudaSuccess) { rsst_set_error("background table kernel failed"); rc = RSST_ECUDA; goto fail; }
     }
@@ -411,6 +416,7 @@ static int plain_steps(rsst_handle* h, double dt, int nsteps, cudaStream_t st) {
   a.bg = h->d_bg;
   a.bg_len = h->bg_len;
   a.tab = h->d_tab;
+  a.tabr = h->d_tabr;
   a.tab_len = h->bg_len;
   a.scal = h->d_scal;
   a.flag = h->d_flag;

@@ -31,10 +31,11 @@ struct BatchRun {
   int vert;
 };
 
-template <class C>
+template <class C, int ST>
 __global__ void __launch_bounds__(C::NT) batch_stage_kernel(const BatchRun* __restrict__ runs,
                                                              const int* __restrict__ tile_begin, int nruns,
-                                                             int total_tiles, int stage, int slot) {
+                                                             int total_tiles, int slot) {
+  constexpr int stage = ST;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   uint64_t* bar = t2_barrier<C>(smem_raw);
   float* sdt = reinterpret_cast<float*>(bar + 1);
@@ -76,8 +77,8 @@ __global__ void __launch_bounds__(C::NT) batch_stage_kernel(const BatchRun* __re
     const CUtensorMap* map = &br.tmap[stage == 1 ? 0 : 1];
     float rmax = 0.0f;
     bool ok = true;
-    const bool fine = br.vert == 1 ? tile2d_f<C, 1>(map, *sr, *sdt, tx, ty, smem_raw, phase, rmax, ok)
-                                   : tile2d_f<C, -1>(map, *sr, *sdt, tx, ty, smem_raw, phase, rmax, ok);
+    const bool fine = br.vert == 1 ? tile2d_f<C, 1, -1, -1, ST>(map, *sr, *sdt, tx, ty, smem_raw, phase, rmax, ok)
+                                   : tile2d_f<C, -1, -1, -1, ST>(map, *sr, *sdt, tx, ty, smem_raw, phase, rmax, ok);
     if (!fine) {
       // A bounded wait gave up (the tile routine has already waited for its
       // copy).  This block leaves the rest of the stage: every run that owns
@@ -146,18 +147,18 @@ static PFN_cuTensorMapEncodeTiled_v12000 batch_encoder() {
 }
 
 template <class C>
-static void* kernel_of() {
-  return (void*)batch_stage_kernel<C>;
+static void* kernel_of(int stage) {
+  return stage == 1 ? (void*)batch_stage_kernel<C, 1> : (void*)batch_stage_kernel<C, 2>;
 }
 
-static void* cand_kernel(int c, int* nt, size_t* smem) {
+static void* cand_kernel(int c, int* nt, size_t* smem, int stage = 1) {
   switch (c) {
-    case 0: *nt = TC0::NT; *smem = TC0::smem_bytes(); return kernel_of<TC0>();
-    case 1: *nt = TC1::NT; *smem = TC1::smem_bytes(); return kernel_of<TC1>();
-    case 2: *nt = TC2::NT; *smem = TC2::smem_bytes(); return kernel_of<TC2>();
-    case 3: *nt = TC3::NT; *smem = TC3::smem_bytes(); return kernel_of<TC3>();
-    case 4: *nt = TC4::NT; *smem = TC4::smem_bytes(); return kernel_of<TC4>();
-    default: *nt = TC5::NT; *smem = TC5::smem_bytes(); return kernel_of<TC5>();
+    case 0: *nt = TC0::NT; *smem = TC0::smem_bytes(); return kernel_of<TC0>(stage);
+    case 1: *nt = TC1::NT; *smem = TC1::smem_bytes(); return kernel_of<TC1>(stage);
+    case 2: *nt = TC2::NT; *smem = TC2::smem_bytes(); return kernel_of<TC2>(stage);
+    case 3: *nt = TC3::NT; *smem = TC3::smem_bytes(); return kernel_of<TC3>(stage);
+    case 4: *nt = TC4::NT; *smem = TC4::smem_bytes(); return kernel_of<TC4>(stage);
+    default: *nt = TC5::NT; *smem = TC5::smem_bytes(); return kernel_of<TC5>(stage);
   }
 }
 
@@ -194,7 +195,7 @@ static int build_descriptors(rsst_batch* b, int c) {
     br.r.g = h->g;
     br.r.p = h->p;
     br.r.pf = h->pf;
-    br.r.tab = h->d_tab;
+    br.r.tabr = h->d_tabr;
     br.r.tab_len = h->bg_len;
     br.r.flag = h->d_flag;
     br.r.stall_ns = h->stall_ns;
@@ -212,8 +213,10 @@ static int build_descriptors(rsst_batch* b, int c) {
   }
   int nt;
   size_t smem;
-  void* k = cand_kernel(c, &nt, &smem);
-  if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+  void* k = cand_kernel(c, &nt, &smem, 2);
+  if (cudaFuncSetAttribute(cand_kernel(c, &nt, &smem, 1), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+          cudaSuccess ||
+      cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
     rsst_set_error("cudaFuncSetAttribute failed for the batch kernel");
     return RSST_ECUDA;
   }
@@ -224,7 +227,14 @@ static int build_descriptors(rsst_batch* b, int c) {
     rsst_set_error("rsst_batch: cannot query the device's SM count");
     return RSST_ECUDA;
   }
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, nt, smem) != cudaSuccess || per_sm < 1) per_sm = 1;
+  int per_sm1 = 0;  // the grid must be resident for both stage kernels
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, nt, smem) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm1, cand_kernel(c, &nt, &smem, 1), nt, smem) != cudaSuccess) {
+    cudaGetLastError();
+    per_sm = 1;
+  }
+  if (per_sm1 < per_sm) per_sm = per_sm1;
+  if (per_sm < 1) per_sm = 1;
   b->grid = sms * per_sm < total ? sms * per_sm : total;
   if (b->grid < 1) b->grid = 1;
   b->total_tiles = total;
@@ -237,14 +247,22 @@ static int launch_stage(rsst_batch* b, int stage, int slot) {
   int nt;
   size_t smem;
   cand_kernel(b->choice, &nt, &smem);
+#define RSST_BATCH_LAUNCH(C)                                                                              \
+  if (stage == 1)                                                                                         \
+    batch_stage_kernel<C, 1><<<b->grid, nt, smem, b->stream>>>(b->d_runs, b->d_tile_begin, b->nruns,      \
+                                                               b->total_tiles, slot);                     \
+  else                                                                                                    \
+    batch_stage_kernel<C, 2><<<b->grid, nt, smem, b->stream>>>(b->d_runs, b->d_tile_begin, b->nruns,      \
+                                                               b->total_tiles, slot);
   switch (b->choice) {
-    case 0: batch_stage_kernel<TC0><<<b->grid, nt, smem, b->stream>>>(b->d_runs, b->d_tile_begin, b->nruns, b->total_tiles, stage, slot); break;
-    case 1: batch_stage_kernel<TC1><<<b->grid, nt, smem, b->stream>>>(b->d_runs, b->d_tile_begin, b->nruns, b->total_tiles, stage, slot); break;
-    case 2: batch_stage_kernel<TC2><<<b->grid, nt, smem, b->stream>>>(b->d_runs, b->d_tile_begin, b->nruns, b->total_tiles, stage, slot); break;
-    case 3: batch_stage_kernel<TC3><<<b->grid, nt, smem, b->stream>>>(b->d_runs, b->d_tile_begin, b->nruns, b->total_tiles, stage, slot); break;
-    case 4: batch_stage_kernel<TC4><<<b->grid, nt, smem, b->stream>>>(b->d_runs, b->d_tile_begin, b->nruns, b->total_tiles, stage, slot); break;
-    default: batch_stage_kernel<TC5><<<b->grid, nt, smem, b->stream>>>(b->d_runs, b->d_tile_begin, b->nruns, b->total_tiles, stage, slot); break;
+    case 0: RSST_BATCH_LAUNCH(TC0) break;
+    case 1: RSST_BATCH_LAUNCH(TC1) break;
+    case 2: RSST_BATCH_LAUNCH(TC2) break;
+    case 3: RSST_BATCH_LAUNCH(TC3) break;
+    case 4: RSST_BATCH_LAUNCH(TC4) break;
+    default: RSST_BATCH_LAUNCH(TC5) break;
   }
+#undef RSST_BATCH_LAUNCH
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
     rsst_set_error("batch stage launch: %s", cudaGetErrorString(e));

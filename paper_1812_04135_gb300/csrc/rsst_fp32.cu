@@ -21,19 +21,30 @@ namespace rsst {
 // ---------------------------------------------------------------------------
 
 template <int NV, int V>
-__global__ void bgtab_kernel(const double* __restrict__ bg, int L, Phys p, float* __restrict__ tab) {
+__global__ void bgtab_kernel(const double* __restrict__ bg, int L, Phys p, float* __restrict__ tab,
+                             float* __restrict__ tabr) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= L) return;
   const double* r0 = bg;
   const double* e0 = bg + L;
   auto U0 = [&](int kk, int c) -> double { return c == 0 ? r0[kk] : e0[kk]; };
   auto put = [&](int f, double v) { tab[(size_t)f * L + k] = (float)v; };
+  auto putr = [&](int f, double v) {
+    if (tabr) tabr[(size_t)k * TR_W + f] = (float)v;
+  };
   for (int f = 0; f < TB_COUNT; ++f) put(f, 0.0);
+  for (int f = 0; f < TR_W; ++f) putr(f, 0.0);
+  // gx P/rho is (a/xi)^2 for a constant xi and a^2 under the C_max law
+  const double gx = p.use_cmax ? p.gamma : p.gamma_xi2;
   const double P0 = p.gm1 * e0[k];
   put(TB_RHO0, r0[k]);
   put(TB_E0, e0[k]);
   put(TB_P0, P0);
   put(TB_H0, e0[k] + P0);
+  putr(TR_RHO0, r0[k]);
+  putr(TR_P0, P0);
+  putr(TR_GXP0, gx * P0);
+  putr(TR_H0, e0[k] + P0);
   auto slope = [&](int kk, int c) { return mc_slope(U0(kk, c) - U0(kk - 1, c), U0(kk + 1, c) - U0(kk, c)); };
   if (k >= 1 && k <= L - 2) {
     for (int c = 0; c < 2; ++c) {
@@ -45,6 +56,13 @@ __global__ void bgtab_kernel(const double* __restrict__ bg, int L, Phys p, float
       put(TB_S + 6 * c + 3, 2.0 * dL - s0);
       put(TB_S + 6 * c + 4, 2.0 * dR - s0);
       put(TB_S + 6 * c + 5, 0.5 * (dL + dR) - s0);
+      const int b = c == 0 ? TR_SRHO : TR_SE;  // half slopes: the face states are U +- slope/2
+      putr(b + 0, dL);
+      putr(b + 1, dR);
+      putr(b + 2, 0.5 * (0.0 - s0));
+      putr(b + 3, 0.5 * (2.0 * dL - s0));
+      putr(b + 4, 0.5 * (2.0 * dR - s0));
+      putr(b + 5, 0.5 * (0.5 * (dL + dR) - s0));
     }
   }
   // background face state of the face between padded cells kk-1 and kk
@@ -75,6 +93,22 @@ __global__ void bgtab_kernel(const double* __restrict__ bg, int L, Phys p, float
     put(TB_FALPHA, cL >= cR ? cL : cR);
     put(TB_FDRHO, qR[0] - qL[0]);
     put(TB_FDE, qR[NV - 1] - qL[NV - 1]);
+    putr(TR_FL + 0, qL[0]);
+    putr(TR_FL + 1, PL);
+    putr(TR_FL + 2, gx * PL);
+    putr(TR_FL + 3, qL[NV - 1] + PL);
+    putr(TR_FR + 0, qR[0]);
+    putr(TR_FR + 1, PR);
+    putr(TR_FR + 2, gx * PR);
+    putr(TR_FR + 3, qR[NV - 1] + PR);
+    putr(TR_FA0X + 0, aL * p.inv_xi);
+    putr(TR_FA0X + 1, aR * p.inv_xi);
+    putr(TR_FA0X + 2, gx / qL[0]);
+    putr(TR_FA0X + 3, gx / qR[0]);
+    putr(TR_FG, cL - cR);
+    putr(TR_FALPHA, cL >= cR ? cL : cR);
+    putr(TR_FJRHO, qR[0] - qL[0]);
+    putr(TR_FJE, qR[NV - 1] - qL[NV - 1]);
   }
   if (k >= 2 && k <= L - 3) {
     double qL[NV], qR[NV], Fm[NV], Fp[NV];
@@ -87,10 +121,14 @@ __global__ void bgtab_kernel(const double* __restrict__ bg, int L, Phys p, float
     put(TB_D0RHO, D0[0]);
     put(TB_D0MV, D0[1 + V]);
     put(TB_D0E, D0[NV - 1]);
+    putr(TR_D0RHO, D0[0]);
+    putr(TR_D0MV, D0[1 + V]);
+    putr(TR_D0E, D0[NV - 1]);
     for (int v = 0; v < NV; ++v) {
       double R = D0[v];
       if (v >= 1 && v <= NV - 2) R += r0[k] * p.grav[v - 1];
       put(TB_R0 + v, R);
+      putr(TR_R0 + v, R);
     }
   }
 }
@@ -618,10 +656,11 @@ int rsst_launch_stage_fp32(const StageArgs<float>& a, cudaStream_t s) {
   return RSST_EINVAL;
 }
 
-int rsst_launch_bgtab(const double* bg, int bg_len, const Geom& g, const Phys& p, float* tab, cudaStream_t s) {
+int rsst_launch_bgtab(const double* bg, int bg_len, const Geom& g, const Phys& p, float* tab, float* tabr,
+                      cudaStream_t s) {
   const int blocks = (bg_len + 127) / 128;
   const int nv = g.ndim + 2, V = p.vertical;
-#define BG(NVv, Vv) bgtab_kernel<NVv, Vv><<<blocks, 128, 0, s>>>(bg, bg_len, p, tab)
+#define BG(NVv, Vv) bgtab_kernel<NVv, Vv><<<blocks, 128, 0, s>>>(bg, bg_len, p, tab, tabr)
   if (nv == 3) BG(3, 0);
   else if (nv == 4) { if (V == 0) BG(4, 0); else BG(4, 1); }
   else { if (V == 0) BG(5, 0); else if (V == 1) BG(5, 1); else BG(5, 2); }

@@ -1,8 +1,22 @@
 // 2D float32 perturbation tile routine (see rsst_fp32_2d.cu for the layout).
+//
+// The state is U = U0 + U1, U0 = (rho0, 0, 0, E0) a float64 background that
+// varies along y only (or is absent), U1 the stored float32 perturbation.
+// Every term that feeds an update is formed from perturbation-sized
+// quantities (see rsst_math_fp32.cuh for the splitting), with the arithmetic
+// arranged for few instructions per cell:
+//  - each cell's MC slope is computed once per axis, as a half slope h
+//    (face states U +- h); along x a lane hands its cell's right face state
+//    to the next lane by a warp shuffle, along y the column march carries it;
+//  - faces hold twice the LLF flux, 2F = F(qL) + F(qR) - alpha (qR - qL),
+//    and the exact 1/2 folds into 1/dx;
+//  - the background enters through one row-major table row per vertical
+//    index, read as float4 (broadcast: all lanes of a warp share the row).
 #pragma once
 
 #include "rsst_common.cuh"
 #include "rsst_internal.h"
+#include "rsst_fp32_lean.cuh"
 #include "rsst_math_fp32.cuh"
 #include "rsst_tma.cuh"
 
@@ -21,16 +35,23 @@ struct T2Cfg {
   static constexpr int FXW = BX + 1;   // x faces per row
   static constexpr int U_FLOATS = NV * SYP * SXP;
   static constexpr int FX_FLOATS = NV * BY * FXW;
-  static constexpr int TAB_FLOATS = TB_COUNT * SYP;
+  static constexpr int TAB_FLOATS = TR_W * SYP;
   static constexpr size_t SCRATCH = (size_t)(U_FLOATS + FX_FLOATS + TAB_FLOATS) * 4;
+  // x-face pass: the slope cells -1 .. BX of every row, in one flat list
+  // walked by warps in chunks of 32 cells that overlap by one
+  static constexpr int CW = BX + 2;
+  static constexpr int NCHUNK = (BY * CW - 1 + 30) / 31;
   static constexpr uint32_t BOX_BYTES = U_FLOATS * 4;
   static constexpr size_t smem_bytes() { return SCRATCH + 16 + 8 * 8 + 512 + 128; }
   static_assert(BY % SEG == 0, "column segments must tile BY");
+  static_assert(BX % 32 == 0, "a warp of the column march covers 32 columns of one segment");
+  static_assert((U_FLOATS + FX_FLOATS) % 4 == 0, "the table rows start on a 16-byte boundary");
+  static_assert(NT % 32 == 0, "whole warps");
   static_assert(SCRATCH % 8 == 0, "the barriers after the scratch area need 8-byte alignment");
   static_assert(SXP <= 256 && SYP <= 256, "TMA box dimensions are at most 256");
 };
 
-using T2 = T2Cfg<128, 8, 8>;  // single-run default (best of a 13-shape sweep on GB300: 5 CTAs of 4 warps per SM)
+using T2 = T2Cfg<128, 8, 8>;  // single-run default
 
 template <class C>
 __device__ __forceinline__ uint64_t* t2_barrier(unsigned char* smem) {
@@ -58,105 +79,31 @@ struct TileRun {
   PhysF pf;
   const float* base;
   float* out;
-  const float* tab;
+  const float* tabr;  // row-major background table, or null (no background)
   int tab_len;
   unsigned int* flag;
   int stage;
   int64_t stall_ns;  // > 0 only in failure-detection tests (see tile2d_f)
 };
 
-// LLF flux of the x face between tile cells with smem columns c-1 | c (row sr).
-template <class T2, int VERT>
-__device__ __forceinline__ void t2_xflux(const float* __restrict__ sU, const float* __restrict__ st, int sr, int c,
-                                         const PhysF& pf, float (&F)[4]) {
-  constexpr int NV = 4;
-  float qL[NV], qR[NV];
-#pragma unroll
-  for (int v = 0; v < NV; ++v) {
-    const float* row = sU + (v * T2::SYP + sr) * T2::SXP + c;
-    const float um2 = row[-2], um1 = row[-1], u0 = row[0], up1 = row[1];
-    qL[v] = um1 + 0.5f * mc_slope_f(um1 - um2, u0 - um1);
-    qR[v] = u0 - 0.5f * mc_slope_f(u0 - um1, up1 - u0);
-  }
-  float FL[NV], FR[NV], cL, cR, dum;
-  if constexpr (VERT < 0) {
-    euler_flux_f<NV, 0>(qL, pf, FL, cL);
-    euler_flux_f<NV, 0>(qR, pf, FR, cR);
-  } else {
-    const float rho0 = st[TB_RHO0 * T2::SYP + sr], P0 = st[TB_P0 * T2::SYP + sr], H0 = st[TB_H0 * T2::SYP + sr];
-    pert_flux_f<NV, 0, false>(qL, rho0, P0, H0, 0.0f, pf, FL, cL, dum);
-    pert_flux_f<NV, 0, false>(qR, rho0, P0, H0, 0.0f, pf, FR, cR, dum);
-  }
-  const float alpha = cL >= cR ? cL : cR;
-#pragma unroll
-  for (int v = 0; v < NV; ++v) F[v] = 0.5f * (FL[v] + FR[v]) - 0.5f * alpha * (qR[v] - qL[v]);
-}
-
-// MC slope along y of the cell at smem row r from its neighbours' values.
-template <class T2, int VERT>
-__device__ __forceinline__ void t2_yslope(const float (&um)[4], const float (&u0)[4], const float (&up)[4],
-                                          const float* __restrict__ st, int r, float (&s)[4]) {
-#pragma unroll
-  for (int v = 0; v < 4; ++v) {
-    const float da = u0[v] - um[v], db = up[v] - u0[v];
-    if (VERT == 1 && (v == 0 || v == 3))
-      s[v] = bg_slope_f(st + (TB_S + 6 * (v == 0 ? 0 : 1)) * T2::SYP, T2::SYP, r, da, db);
-    else
-      s[v] = mc_slope_f(da, db);
-  }
-}
-
-// y-face flux between cells (u0, s0) below and (u1, s1) above; face table at smem row rf.
-template <class T2, int VERT>
-__device__ __forceinline__ void t2_yflux(const float (&u0)[4], const float (&s0)[4], const float (&u1)[4],
-                                         const float (&s1)[4], const float* __restrict__ st, int rf, const PhysF& pf,
-                                         float (&F)[4]) {
-  constexpr int NV = 4;
-  float qL[NV], qR[NV];
-#pragma unroll
-  for (int v = 0; v < NV; ++v) {
-    qL[v] = u0[v] + 0.5f * s0[v];
-    qR[v] = u1[v] - 0.5f * s1[v];
-  }
-  float FL[NV], FR[NV], cL, cR;
-  if constexpr (VERT < 0) {
-    euler_flux_f<NV, 1>(qL, pf, FL, cL);
-    euler_flux_f<NV, 1>(qR, pf, FR, cR);
-    const float alpha = cL >= cR ? cL : cR;
-#pragma unroll
-    for (int v = 0; v < NV; ++v) F[v] = 0.5f * (FL[v] + FR[v]) - 0.5f * alpha * (qR[v] - qL[v]);
-  } else {
-    float dcL, dcR;
-    const float gdiff = st[TB_FG * T2::SYP + rf], al0 = st[TB_FALPHA * T2::SYP + rf];
-    const float c0L = gdiff >= 0.0f ? al0 : al0 + gdiff, c0R = gdiff >= 0.0f ? al0 - gdiff : al0;
-    pert_flux_f<NV, 1, true>(qL, st[TB_FRHOL * T2::SYP + rf], st[TB_FPL * T2::SYP + rf], st[TB_FHL * T2::SYP + rf],
-                             st[TB_FAL * T2::SYP + rf], pf, FL, cL, dcL, c0L);
-    pert_flux_f<NV, 1, true>(qR, st[TB_FRHOR * T2::SYP + rf], st[TB_FPR * T2::SYP + rf], st[TB_FHR * T2::SYP + rf],
-                             st[TB_FAR * T2::SYP + rf], pf, FR, cR, dcR, c0R);
-    const float dalpha = gdiff >= 0.0f ? fmaxf(dcL, dcR - gdiff) : fmaxf(dcL + gdiff, dcR);
-    const float alpha = st[TB_FALPHA * T2::SYP + rf] + dalpha;
-    const float jr = st[TB_FDRHO * T2::SYP + rf], je = st[TB_FDE * T2::SYP + rf];
-#pragma unroll
-    for (int v = 0; v < NV; ++v) {
-      const float j0v = v == 0 ? jr : (v == NV - 1 ? je : 0.0f);
-      F[v] = 0.5f * (FL[v] + FR[v]) - 0.5f * (alpha * (qR[v] - qL[v]) + dalpha * j0v);
-    }
-  }
-}
-
-// Process tile (tx, ty) of run r: returns false if the TMA wait timed out
-// (flag set).  Accumulates the stage-2 CFL rate maximum and physical check.
-// The caller initialised the barrier; `phase` is its current parity.
-template <class T2, int VERT>
+// Process tile (tx, ty) of run r: returns false if a bounded wait gave up
+// (flag set, nothing left in flight).  Accumulates the stage-2 CFL rate
+// maximum and physical check.  The caller initialised the barrier; `phase` is
+// its current parity.  FORM, CM and ST fix the form, the C_max law and the
+// stage at compile time (-1, -1, 0: read from the run).
+template <class T2, int VERT, int FORM, int CM, int ST>
 __device__ __forceinline__ bool tile2d_f(const CUtensorMap* tin, const TileRun& r, float dt, int tx, int ty,
                                          unsigned char* smem, uint32_t& phase, float& rmax, bool& ok_all) {
   constexpr int NV = 4;
+  constexpr bool BG = VERT >= 0;
+  constexpr int PL = T2::SYP * T2::SXP;  // floats per field in the box
   float* sU = reinterpret_cast<float*>(smem);
   float* sFx = sU + T2::U_FLOATS;
-  float* st = sFx + T2::FX_FLOATS;
+  float* st = sFx + T2::FX_FLOATS;  // table rows of padded y j0 .. j0 + SYP - 1
   uint64_t* bar = t2_barrier<T2>(smem);
   const Geom& g = r.g;
   const PhysF& pf = r.pf;
+  const int stage = ST > 0 ? ST : r.stage;
   const int i0 = tx * T2::BX, j0 = ty * T2::BY;
   const int tid = threadIdx.x;
 
@@ -166,12 +113,14 @@ __device__ __forceinline__ bool tile2d_f(const CUtensorMap* tin, const TileRun& 
     mbar_expect_tx(bar, T2::BOX_BYTES);
     tma_load_3d(sU, tin, bar, i0 + g.xoff - T2::XO, j0, 0);
   }
-  if constexpr (VERT >= 0) {
-    for (int id = tid; id < T2::TAB_FLOATS; id += T2::NT) {
-      const int f = id / T2::SYP, rr = id - f * T2::SYP;
-      const int kp = j0 + rr;
-      st[id] = kp < r.tab_len ? r.tab[(size_t)f * r.tab_len + kp] : 0.0f;
-    }
+  if constexpr (BG) {
+    // SYP consecutive table rows (16-byte aligned) as float4
+    const float4* src = reinterpret_cast<const float4*>(r.tabr);
+    float4* dst = reinterpret_cast<float4*>(st);
+    constexpr int N4 = T2::TAB_FLOATS / 4;
+    const int first4 = j0 * (TR_W / 4), last4 = r.tab_len * (TR_W / 4);
+    for (int id = tid; id < N4; id += T2::NT)
+      dst[id] = first4 + id < last4 ? src[first4 + id] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
   }
   // the give-up decision is taken by the whole block (no thread may leave
   // while others wait at a barrier); a late copy gets one more bounded wait
@@ -184,7 +133,7 @@ __device__ __forceinline__ bool tile2d_f(const CUtensorMap* tin, const TileRun& 
   if (r.stall_ns > 0) {
     // Failure-detection test: with the tile's copy landed (nothing in
     // flight), wait on a barrier that expects 16 bytes no copy delivers, so
-    // the bounded wait runs out and the give-up path above is taken.
+    // the bounded wait runs out and the give-up path is taken.
     uint64_t* sb = t2_stall_barrier<T2>(smem);
     if (tid == 0) {
       mbar_init(sb, 1);
@@ -198,86 +147,156 @@ __device__ __forceinline__ bool tile2d_f(const CUtensorMap* tin, const TileRun& 
     }
   }
 
-  // x faces
   const int nx = g.n[0], ny = g.n[1];
-  for (int fid = tid; fid < T2::BY * T2::FXW; fid += T2::NT) {
-    const int row = fid / T2::FXW;
-    const int fx = fid - row * T2::FXW;
-    if (i0 + fx > nx || j0 + row >= ny) continue;
-    float F[NV];
-    t2_xflux<T2, VERT>(sU, st, row + 2, fx + T2::XO, pf, F);
+  const int lane = tid & 31;
+  // ---- x faces.  The slope cells -1 .. BX of every row form one flat list;
+  // chunk k holds cells 31k .. 31k + 31 (lane l: cell 31k + l).  Each lane
+  // takes its cell's half slope: its right state U - h is the right state of
+  // the face on the cell's left, and U + h, passed one lane up, the left
+  // state of that face for the next lane.  Lanes 1..31 thus get every face
+  // of the row (faces 0 .. BX), no lane recomputes a slope, and no lane runs
+  // alone; a lane whose two cells lie in different rows has no face.
+  {
+    const int nwarp = T2::NT / 32;
+    for (int k = tid >> 5; k < T2::NCHUNK; k += nwarp) {
+      int F = 31 * k + lane;
+      const bool inb = F < T2::BY * T2::CW;
+      F = inb ? F : T2::BY * T2::CW - 1;  // keeps the loads inside the box
+      const int row = F / T2::CW;
+      const int cc = F - row * T2::CW - 1;  // tile column -1 .. BX
+      const int sr = row + 2;
+      const float* ur = sU + sr * T2::SXP + T2::XO + cc;
+      float qR[NV], qL[NV];
 #pragma unroll
-    for (int v = 0; v < NV; ++v) sFx[(v * T2::BY + row) * T2::FXW + fx] = F[v];
+      for (int v = 0; v < NV; ++v) {
+        const float* uv = ur + v * PL;
+        const float um = uv[-1], u0 = uv[0], up = uv[1];
+        const float h = half_mc_f(u0 - um, up - u0);
+        qR[v] = u0 - h;
+        qL[v] = __shfl_up_sync(0xffffffffu, u0 + h, 1);
+      }
+      float4 cb = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+      if constexpr (BG) cb = *reinterpret_cast<const float4*>(st + sr * TR_W + TR_RHO0);
+      float G[NV];
+      face_flat_cm<NV, 0, BG, CM>(qL, qR, cb, pf, G);
+      if (inb && lane > 0 && cc >= 0 && i0 + cc <= nx && j0 + row < ny) {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) sFx[(v * T2::BY + row) * T2::FXW + cc] = G[v];
+      }
+    }
   }
   __syncthreads();
 
-  // column march with the fused epilogue
+  // ---- column march with the fused epilogue: each thread owns tile column
+  // col, rows jb .. jb + SEG - 1; a register window carries the cell states,
+  // the y half slope and the lower face's flux.
   const int col = tid % T2::BX;
-  const int seg = tid / T2::BX;
+  const int jb = (tid / T2::BX) * T2::SEG;
   const int x = i0 + col;
-  const int jb = seg * T2::SEG;  // first tile row of this thread
   if (x < nx && j0 + jb < ny) {
-    const int sc = col + T2::XO;
-    auto ld = [&](int srow, float (&u)[4]) {
+    const float* uc = sU + T2::XO + col;
+    auto ld = [&](int srow, float (&u)[NV]) {
 #pragma unroll
-      for (int v = 0; v < NV; ++v) u[v] = sU[(v * T2::SYP + srow) * T2::SXP + sc];
+      for (int v = 0; v < NV; ++v) u[v] = uc[v * PL + srow * T2::SXP];
     };
-    float um[4], u0[4], u1[4], u2[4], s0[4], s1[4], sm[4], Fm[4], Fp[4];
-    // cells jb-2 .. jb+1 live at smem rows jb .. jb+3
-    ld(jb, u2);   // u2 used as scratch for cell jb-2
-    ld(jb + 1, um);
-    ld(jb + 2, u0);
-    ld(jb + 3, u1);
-    t2_yslope<T2, VERT>(u2, um, u0, st, jb + 1, sm);   // slope of cell jb-1
-    t2_yslope<T2, VERT>(um, u0, u1, st, jb + 2, s0);   // slope of cell jb
-    t2_yflux<T2, VERT>(um, sm, u0, s0, st, jb + 2, pf, Fm);
-    const float idx = pf.inv_dx[0], idy = pf.inv_dx[1];
+    float u0[NV], u1[NV], h0[NV], Fm[NV];
+    {
+      float umm[NV], um[NV], hm[NV];
+      // cells jb-2 .. jb+1 live at smem rows jb .. jb+3
+      ld(jb, umm);
+      ld(jb + 1, um);
+      ld(jb + 2, u0);
+      ld(jb + 3, u1);
+      vslope_f<NV, BG>(umm, um, u0, st + (jb + 1) * TR_W, hm);  // cell jb-1
+      vslope_f<NV, BG>(um, u0, u1, st + (jb + 2) * TR_W, h0);   // cell jb
+      float qL[NV], qR[NV];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        qL[v] = um[v] + hm[v];
+        qR[v] = u0[v] - h0[v];
+      }
+      face_vert_cm<NV, 1, BG, CM>(qL, qR, st + (jb + 2) * TR_W, pf, Fm);
+    }
+    const float idx = 0.5f * pf.inv_dx[0], idy = 0.5f * pf.inv_dx[1];  // the faces hold 2F
     const int64_t fs = g.fstride;
+    const bool xghost = x < RSST_G || x >= nx - RSST_G;
+    const int64_t o0 = pidx(g, x, j0 + jb, 0);
+    // stage 2: U^n of the next row's cell is loaded one row ahead, so its
+    // global-memory latency overlaps a row of arithmetic
+    float bnext[NV] = {0.0f, 0.0f, 0.0f, 0.0f};
+    if (stage == 2) {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) bnext[v] = r.base[v * fs + o0];
+    }
 #pragma unroll 1
     for (int jj = 0; jj < T2::SEG; ++jj) {
-      const int j = jb + jj;       // tile row of the cell
+      const int j = jb + jj;  // tile row of the cell
       if (j0 + j >= ny) break;
-      ld(j + 4, u2);               // cell j+2
-      t2_yslope<T2, VERT>(u0, u1, u2, st, j + 3, s1);   // slope of cell j+1
-      t2_yflux<T2, VERT>(u0, s0, u1, s1, st, j + 3, pf, Fp);
-      float L[4], Dl[4];
+      float bv[NV];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) bv[v] = bnext[v];
+      if (stage == 2 && jj + 1 < T2::SEG && j0 + j + 1 < ny) {
+        const int64_t on = o0 + (int64_t)(jj + 1) * g.pitch;
+#pragma unroll
+        for (int v = 0; v < NV; ++v) bnext[v] = r.base[v * fs + on];
+      }
+      const int sr = j + 2;  // its smem row
+      float u2[NV], h1[NV], Fp[NV];
+      ld(j + 4, u2);                                          // cell j+2
+      vslope_f<NV, BG>(u0, u1, u2, st + (j + 3) * TR_W, h1);  // cell j+1
+      {
+        float qL[NV], qR[NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          qL[v] = u0[v] + h0[v];
+          qR[v] = u1[v] - h1[v];
+        }
+        face_vert_cm<NV, 1, BG, CM>(qL, qR, st + (j + 3) * TR_W, pf, Fp);
+      }
+      float L[NV], Dl[NV];
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
         const float* fr = sFx + (v * T2::BY + j) * T2::FXW + col;
-        L[v] = -(Fp[v] - Fm[v]) * idy - (fr[1] - fr[0]) * idx;
-        Dl[v] = L[v];
+        L[v] = fmaf(-(Fp[v] - Fm[v]), idy, -(fr[1] - fr[0]) * idx);
       }
       float rho0 = 0.0f, P0 = 0.0f;
-      const int srow = j + 2;
-      if constexpr (VERT >= 0) {
-        rho0 = st[TB_RHO0 * T2::SYP + srow];
-        P0 = st[TB_P0 * T2::SYP + srow];
-        Dl[0] += st[TB_D0RHO * T2::SYP + srow];
-        Dl[2] += st[TB_D0MV * T2::SYP + srow];
-        Dl[3] += st[TB_D0E * T2::SYP + srow];
+      if constexpr (BG) {
+        const float* tr = st + sr * TR_W;
+        const float4 cb = *reinterpret_cast<const float4*>(tr + TR_RHO0);
+        const float4 r0 = *reinterpret_cast<const float4*>(tr + TR_R0);
+        const float4 d0 = *reinterpret_cast<const float4*>(tr + TR_R0 + 4);  // R0[4] (unused in 2D), D0 rho, mv, E
+        rho0 = cb.x;
+        P0 = cb.y;
+        Dl[0] = L[0] + d0.y;
+        Dl[1] = L[1];
+        Dl[2] = L[2] + d0.z;
+        Dl[3] = L[3] + d0.w;
+        L[0] += r0.x;
+        L[1] += r0.y;
+        L[2] += r0.z;
+        L[3] += r0.w;
+      } else {
 #pragma unroll
-        for (int v = 0; v < NV; ++v) L[v] += st[(TB_R0 + v) * T2::SYP + srow];
+        for (int v = 0; v < NV; ++v) Dl[v] = L[v];
       }
       const int y = j0 + j;
-      const int64_t o = pidx(g, x, y, 0);
-      float bv[4];
-      if (r.stage == 2) {
-#pragma unroll
-        for (int v = 0; v < NV; ++v) bv[v] = r.base[v * fs + o];
-      }
-      float u[4], rate;
+      const int64_t o = o0 + (int64_t)jj * g.pitch;
+      float u[NV], rate;
       bool ok;
-      cell_update_f<4>(u0, L, Dl, rho0, P0, pf, r.p.variant, r.p.has_grav != 0, r.stage, dt, bv, u, rate, ok);
-      if (r.stage == 2) {
+      cell_lean<NV, FORM, CM, ST>(u0, L, Dl, rho0, P0, pf, r.p.variant, r.p.has_grav != 0, stage, dt, bv, u, rate,
+                                  ok);
+      if (stage == 2) {
         rmax = fmaxf(rmax, rate);
         ok_all = ok_all && ok;
       }
-      store_mirror_ghosts<float, 4>(r.out, g, r.p, x, y, 0, u);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) r.out[v * fs + o] = u[v];
+      if (xghost || y < RSST_G || y >= ny - RSST_G) store_mirror_ghosts<float, 4>(r.out, g, r.p, x, y, 0, u);
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
         u0[v] = u1[v];
         u1[v] = u2[v];
-        s0[v] = s1[v];
+        h0[v] = h1[v];
         Fm[v] = Fp[v];
       }
     }

@@ -59,6 +59,9 @@ struct PhysF {
   float grav[3];
   float inv_dx[3];
   float sum_inv_dx;
+  float hgm1;     // (gamma - 1)/2
+  float gam_gm1;  // gamma/(gamma - 1): (e + P)/P of the ideal gas
+  float gx;       // gamma/xi^2 (constant xi: gx P/rho = (a/xi)^2), gamma under the C_max law
 };
 
 // Background tables of the float32 perturbation mode: float32 rows of
@@ -80,6 +83,23 @@ enum BgTab {
   TB_COUNT
 };
 
+// Row-major background table of the TMA float32 kernels: TR_W floats per
+// padded vertical index k (16-byte aligned rows, read as float4).  Cell
+// entries describe padded cell k, face entries the face between padded
+// cells k-1 and k.  Values are computed in float64 and rounded once.
+enum BgRow {
+  TR_RHO0 = 0, TR_P0, TR_GXP0, TR_H0,   // cell: rho0, P0, gx P0, H0 = E0 + P0
+  TR_R0 = 4,                            // cell: background residual L(U0) incl. force, NV entries (5 slots)
+  TR_D0RHO = 9, TR_D0MV, TR_D0E,        // cell: background Euler tendency (rho, m_vertical, E)
+  TR_SRHO = 12,                         // cell: slope rows of rho: d0L, d0R, then half of lin_B(d0) - MC(d0), B = 0..3
+  TR_SE = 18,                           // cell: the same for E
+  TR_FL = 24,                           // face, left state: rho0, P0, gx P0, H0
+  TR_FR = 28,                           // face, right state: rho0, P0, gx P0, H0
+  TR_FA0X = 32,                         // face: a0/xi left, right; gx/rho0 left, right
+  TR_FG = 36, TR_FALPHA, TR_FJRHO, TR_FJE,  // face: c0L - c0R, alpha0, rho0R - rho0L, E0R - E0L
+  TR_W = 40
+};
+
 // Arguments of one fused RK stage launch (single run).
 template <typename T>
 struct StageArgs {
@@ -98,6 +118,7 @@ struct StageArgs {
   PhysF pf;         // float32 constants (float32 kernels)
   const float* tab; // background tables [TB_COUNT][tab_len] (float32 mode), or null
   int tab_len;
+  const float* tabr; // row-major background table [tab_len][TR_W] (TMA float32 kernels), or null
   double* dU_out;   // float64 kernels: if set, the Euler tendency of each interior cell
                     // (padded layout) is written here too (adjoint recompute)
   int64_t stall_ns; // > 0 (failure-detection tests only): each tile of the 2D TMA kernel
@@ -124,7 +145,8 @@ int rsst_launch_cfl_df(const float2* U, const Geom& g, const Phys& p, double* sl
 int rsst_launch_sums_df(const float2* U, const Geom& g, double* partial, double* out, double scale_, cudaStream_t s);
 int rsst_launch_stage2d_tma(const CUtensorMap* tin, const StageArgs<float>& a, cudaStream_t s);
 int rsst_launch_stage3d_tma(const CUtensorMap* tin, const StageArgs<float>& a, cudaStream_t s);
-int rsst_launch_bgtab(const double* bg, int bg_len, const Geom& g, const Phys& p, float* tab, cudaStream_t s);
+int rsst_launch_bgtab(const double* bg, int bg_len, const Geom& g, const Phys& p, float* tab, float* tabr,
+                      cudaStream_t s);
 int rsst_launch_pack_fp32(const double* src, float* dst, const Geom& g, const Phys& p, const double* bg,
                           int bg_len, cudaStream_t s);
 int rsst_launch_unpack_fp32(const float* src, double* dst, const Geom& g, const Phys& p, const double* bg,
@@ -152,6 +174,7 @@ struct rsst_handle {
   double* d_stage;      // caller-layout staging for host transfers
   double* h_small;      // pinned host scratch for small read-backs
   float* d_tab;         // background tables (float32 mode), or null
+  float* d_tabr;        // row-major background table (float32 mode), or null
   PhysF pf;
   int use_tma2d;        // 2D float32 runs use the TMA-staged kernel
   int use_tma3d;        // 3D float32 runs use the TMA z-march kernel

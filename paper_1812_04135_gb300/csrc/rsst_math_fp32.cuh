@@ -22,6 +22,21 @@
 
 namespace rsst {
 
+// Hardware reciprocal and square root approximations (a few ulp), with
+// subnormal inputs and results flushed to zero: the float32 kernels never
+// form subnormal densities, pressures or speeds, and without the flush the
+// compiler wraps each approximation in a rescaling sequence.
+__device__ __forceinline__ float rcp_f(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float sqrt_f(float x) {
+  float y;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
 // Monotonized-central slope (Sec. 4.2), float32, branch-free: the magnitude
 // min(2|a|, 2|b|, |a+b|/2) with the sign of a, zero unless ab > 0.  Equal to
 // the branch-wise form (equal magnitudes of same-sign candidates are equal
