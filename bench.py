@@ -39,6 +39,9 @@ L2_FLUSH_BYTES = 256 << 20
 # algorithm: 2D, per face 122 (+2 div, 4 sqrt), divergence 8, correction +
 # force + RK ~40 (+3 div, 2 sqrt); div and sqrt counted as one operation each.
 FP64_FLOPS_PER_CELL_STAGE_2D = 2 * (122 + 6) + 8 + 45
+FP64_FLOP_COUNT = ("algorithmic float64 operations per 2D cell-stage, counted from the algorithm "
+                   "(bench.py FP64_FLOPS_PER_CELL_STAGE_2D: per face 122 + 2 divisions + 4 square roots, "
+                   "divergence 8, correction + force + RK 45)")
 
 # float64 operations of the discrete adjoint per primal cell-stage (2D, PVS,
 # constant xi), counted the same way from the reverse-mode code: the forward
@@ -66,10 +69,6 @@ def _sources_sha(files):
     return h.hexdigest()[:16]
 
 
-def _traffic_for(args, w):
-    return _traffic_key(f"{args.workload}:{args.precision}:{w['n'][0]}")
-
-
 def _traffic_key(key):
     """DRAM bytes per launch of the dominant kernel from the committed ncu
     summary (profiles/traffic.json), only if its sources are unchanged."""
@@ -90,13 +89,6 @@ def _peaks():
         with open(p) as f:
             return json.load(f), "measured"
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
-
-
-def fp64_peak_tflops(sm_mhz: float) -> float:
-    """GB300 float64 rate from unit counts and clock: 152 SMs x 2 DFMA per SM
-    per clock (2 flops each) x clock; the unit count is the one a float64
-    FMA throughput probe measured on GB300 (1.195 TFLOP/s at ~1.97 GHz)."""
-    return 152 * 2.0 * 2.0 * sm_mhz * 1e6 / 1e12
 
 
 class ClockSampler:
@@ -290,126 +282,112 @@ def bytes_per_cell_stage(w, precision):
     return 2.5 * nvar * (4 if precision == "fp32_pert" else 8)
 
 
-def _time_single(w, precision, steps, warmup, dev, flush_l2):
-    """Device time of `steps` single-run SSP-RK2 steps (events per step)."""
+_FP64_PEAK = {}
+
+
+def fp64_peak_measured(dev):
+    """Float64 FMA throughput of this GPU (TFLOP/s) from the library's probe
+    kernel (rsst_fp64_fma_peak: independent FMA chains on every SM, CUDA
+    events), measured once per process, with the SM clock read during it."""
+    if dev.index not in _FP64_PEAK:
+        from paper_1812_04135_gb300 import rsst
+        with ClockSampler(dev.index) as clk:
+            tf, ms = rsst.rsst_fp64_fma_peak(8000)
+        _FP64_PEAK[dev.index] = (tf, ms, clk.summary().get("sm_mhz"))
+    return _FP64_PEAK[dev.index]
+
+
+def _roof_hbm(w, precision, cells, launch_s, peaks, src, traffic_key):
+    alg = bytes_per_cell_stage(w, precision) * cells
+    gbs = alg / launch_s / 1e9
+    return {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": gbs / peaks["hbm_gbs"], "traffic": _traffic_key(traffic_key) if traffic_key else None,
+            "algorithmic_bytes_per_launch": alg, "peak_source": src}
+
+
+def _roof_alu(flops_per_cell_stage, cells, launch_s, dev, what):
+    tf_peak, _, mhz = fp64_peak_measured(dev)
+    tf = flops_per_cell_stage * cells / launch_s / 1e12
+    return {"bound": "alu", "achieved": tf, "peak": tf_peak, "unit": "TFLOP/s", "frac": tf / tf_peak,
+            "traffic": None, "flops_per_cell_stage": flops_per_cell_stage, "flop_count": what,
+            "peak_source": f"measured: rsst_fp64_fma_peak probe (float64 FMA chains on every SM) at {mhz} MHz"}
+
+
+def measure_single(w, precision, steps, warmup, dev, peaks, src, *, flush_l2=True, traffic_key=None,
+                   alu_flops=None, e2e_steps=None, bound=None, extra=None):
+    """One single-run configuration as a full bench entry: `steps` SSP-RK2
+    steps timed one by one with CUDA events on the launching stream (after
+    `warmup` untimed steps; with flush_l2 a 256 MiB buffer is written between
+    steps, outside the events), SM clocks sampled during the timed region,
+    the HBM roofline of the stage kernel (and the float64 arithmetic roofline
+    when alu_flops is given), and the same steps end to end through the C
+    ABI with the state copied in from and out to pinned host memory."""
     from paper_1812_04135_gb300 import rsst
     stream = torch.cuda.current_stream(dev)
     s = rsst.Solver(w, precision, stream=stream)
-    s.set_state(torch.from_numpy(w["U"]).to(dev))
+    U0 = torch.from_numpy(w["U"]).to(dev)
+    s.set_state(U0)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev) if flush_l2 else None
     for _ in range(warmup):
         s.step(1)
     s.sync()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    l0 = s.launches()
     torch.cuda.synchronize()
-    for k in range(steps):
-        if flush is not None:
-            flush.fill_(float(k))
-        ev[k][0].record(stream)
-        s.step(1)
-        ev[k][1].record(stream)
-    torch.cuda.synchronize()
+    with ClockSampler(dev.index) as clk:
+        for k in range(steps):
+            if flush is not None:
+                flush.fill_(float(k))
+            ev[k][0].record(stream)
+            s.step(1)
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+    launches = s.launches() - l0
     s.sync()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    t = sum(step_ms) / 1e3
+    # end to end: host state in, step, host state out, every step
+    ne = e2e_steps or steps
+    host_in = torch.from_numpy(w["U"]).pin_memory()
+    host_out = torch.empty_like(host_in).pin_memory()
+    rsst.rsst_set_state(s.h, host_in, on_host=True)
+    s.step(1)
+    rsst.rsst_get_state(s.h, host_out, on_host=True)
+    torch.cuda.synchronize()
+    e0 = time.perf_counter()
+    for _ in range(ne):
+        rsst.rsst_set_state(s.h, host_in, on_host=True)
+        s.step(1)
+        rsst.rsst_get_state(s.h, host_out, on_host=True)
+    torch.cuda.synchronize()
+    e_el = time.perf_counter() - e0
     s.close()
-    return sum(a.elapsed_time(b) for a, b in ev) / 1e3
-
-
-def _mode_line(w, precision, t, steps, peaks, extra=None):
+    del flush
     cells = int(np.prod(w["n"]))
     launch_s = t / (2 * steps)
-    gbs = bytes_per_cell_stage(w, precision) * cells / launch_s / 1e9
-    d = {"value": cells * 2 * steps / t, "unit": UNIT, "ms_per_step": t / steps * 1e3, "cells": cells,
-         "hbm_achieved_gbs": gbs, "hbm_frac": gbs / peaks["hbm_gbs"]}
+    hbm = _roof_hbm(w, precision, cells, launch_s, peaks, src, traffic_key)
+    d = {"value": cells * 2 * steps / t, "unit": UNIT, "steps": steps, "warmup": warmup,
+         "ms_per_step": t / steps * 1e3, "step_ms_median": statistics.median(step_ms), "cells": cells,
+         "roofline": hbm, "clocks": clk.summary(), "gpu_launches": launches,
+         "l2": "256 MiB buffer written between timed steps" if flush_l2 else "state larger than L2",
+         "e2e": {"value": cells * 2 * ne / e_el, "unit": UNIT, "steps": ne,
+                 "h2d_bytes_per_step": host_in.numel() * 8, "d2h_bytes_per_step": host_out.numel() * 8}}
+    if alu_flops:
+        d["roofline"] = _roof_alu(alu_flops[0], cells, launch_s, dev, alu_flops[1])
+        d["roofline"]["hbm"] = {k: hbm[k] for k in ("achieved", "peak", "frac", "traffic", "unit")}
+    if bound:
+        d["bound"] = bound
     if extra:
         d.update(extra)
     return d
 
 
-def run_modes(dev, peaks, sm_mhz):
-    """The other measured configurations, briefly, for the same JSON line."""
-    from paper_1812_04135_gb300 import inputs, rsst
-    out = {}
-    w = inputs.shear_layer_2d(512, 512, xi=30.0, variant="pvs")
-    out["fp32_pert_shear_512"] = _mode_line(w, "fp32_pert", _time_single(w, "fp32_pert", 20, 3, dev, True), 20, peaks,
-                                            {"bound": "hbm (instruction-issue limited)"})
-    w = inputs.shear_layer_2d(2048, 2048, xi=30.0, variant="pvs")
-    out["fp32_pert_shear_2048"] = _mode_line(w, "fp32_pert", _time_single(w, "fp32_pert", 20, 3, dev, False), 20, peaks,
-                                             {"bound": "hbm (instruction-issue limited)"})
-    w = inputs.shear_layer_2d(512, 512, xi=30.0, variant="pvs")
-    out["fp64_df_shear_512"] = _mode_line(w, "fp64", _time_single(w, "fp64_df", 20, 3, dev, True), 20, peaks,
-                                          {"bound": "alu (float32 pipe, double-float arithmetic)",
-                                           "dtype": "f32x2 double-float (48-bit significand), parity 1e-10 vs f64"})
-    w = inputs.polytrope_3d(variant="pvs")
-    t = _time_single(w, "fp64", 5, 2, dev, False)
-    out["fp64_polytrope_3d"] = _mode_line(w, "fp64", t, 5, peaks, {"bound": "alu (float64)"})
-    out["fp64_df_polytrope_3d"] = _mode_line(w, "fp64", _time_single(w, "fp64_df", 10, 2, dev, False), 10, peaks,
-                                             {"bound": "alu (float32 pipe, double-float arithmetic)",
-                                              "dtype": "f32x2 double-float (48-bit significand), parity 1e-10 vs f64"})
-    out["fp32_pert_polytrope_3d"] = _mode_line(w, "fp32_pert", _time_single(w, "fp32_pert", 20, 3, dev, False), 20,
-                                               peaks, {"bound": "hbm (instruction-issue limited)"})
-    # 1D N=256 sound wave, 2000 steps: launch-bound; CUDA-graph blocks vs plain launches
-    w = inputs.sound_wave_1d(256, xi=10.0, variant="pvs")
-    for k, name in ((16, "fp64_sound1d_256_graph"), (0, "fp64_sound1d_256_plain")):
-        stream = torch.cuda.current_stream(dev)
-        s = rsst.Solver(w, "fp64", stream=stream)
-        s.set_graph_steps(k)
-        s.set_state(torch.from_numpy(w["U"]).to(dev))
-        s.step(64)
-        s.sync()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        s.step(2000)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        s.sync()
-        s.close()
-        t = e0.elapsed_time(e1) / 1e3
-        out[name] = {"value": 256 * 2 * 2000 / t, "unit": UNIT, "steps_per_s": 2000 / t, "steps": 2000,
-                     "graph_steps": k, "bound": "launch latency"}
-    # 2D 4096^2 shear layer: the HBM-regime point of the 2D configuration
-    w = inputs.shear_layer_2d(4096, 4096, xi=30.0, variant="pvs")
-    out["fp64_shear_4096"] = _mode_line(w, "fp64", _time_single(w, "fp64", 3, 2, dev, False), 3, peaks,
-                                        {"bound": "alu (float64)"})
-    out["fp32_pert_shear_4096"] = _mode_line(w, "fp32_pert", _time_single(w, "fp32_pert", 10, 3, dev, False), 10,
-                                             peaks, {"bound": "hbm (instruction-issue limited)"})
-    out["fp64_df_shear_4096"] = _mode_line(w, "fp64", _time_single(w, "fp64_df", 5, 2, dev, False), 5, peaks,
-                                           {"bound": "alu (float32 pipe, double-float arithmetic)",
-                                            "dtype": "f32x2 double-float (48-bit significand), parity 1e-10 vs f64"})
-    del w
-    # adjoint: 2D 256^2 stratified box, 400 steps, checkpoint every 20
-    w = inputs.polytrope_2d(256, 256, xi=20.0, contrast=20.0, amp=1e-3)
-    s = rsst.Solver(w, "fp64", stream=torch.cuda.current_stream(dev))
-    s.set_state(torch.from_numpy(w["U"]).to(dev))
-    dt = s.dt()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    rsst.rsst_adjoint_record(s.h, dt, 400, 20)
-    torch.cuda.synchronize()
-    t_fwd = time.perf_counter() - t0
-    gN = torch.empty((4, 256, 256), dtype=torch.float64, device=dev)
-    rsst.rsst_kinetic_energy(s.h, gN)
-    t0 = time.perf_counter()
-    dxi = 0.0
-    for seg in reversed(range(rsst.rsst_adjoint_segments(s.h))):
-        dxi += rsst.rsst_adjoint_step(s.h, seg, gN)
-    torch.cuda.synchronize()
-    t_rev = time.perf_counter() - t0
-    s.close()
-    cells = 256 * 256
-    out["adjoint_fp64_polytrope_256"] = {
-        "value": cells * 2 * 400 / (t_fwd + t_rev), "unit": UNIT + " (forward record + reverse sweep)",
-        "forward_s": t_fwd, "reverse_s": t_rev, "reverse_over_forward": t_rev / t_fwd,
-        "steps": 400, "checkpoint_every": 20, "dJ_dxi": dxi}
-    return out
-
-
-def run_batched(args, world, rank, local):
+def measure_batched(dev, peaks, src, steps=20, warmup=3, world=1):
     """64 independent float32-perturbation shear layers of uneven size, xi and
-    density ratio: one persistent kernel per stage (graph-captured) vs one
-    launch pair per run per step.  The 64 states total ~0.64 GB (> L2)."""
+    density ratio (2.5e7 cells, 0.8 GB of state: inputs larger than L2): one
+    persistent kernel per stage over all runs' tiles (graph-captured) against
+    one launch pair per run per step, tile shape from the autotuner."""
     from paper_1812_04135_gb300 import inputs, rsst
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
     ws = inputs.batched_runs(count=64, seed=4)
     cells = sum(int(np.prod(w["n"])) for w in ws)
     b = rsst.BatchSolver(ws)
@@ -420,13 +398,13 @@ def run_batched(args, world, rank, local):
     stream = b.stream
 
     def timed(fn):
-        for _ in range(args.warmup):
+        for _ in range(warmup):
             fn(1)
         b.sync()
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
         _barrier(world)
         torch.cuda.synchronize()
-        for k in range(args.steps):
+        for k in range(steps):
             ev[k][0].record(stream)
             fn(1)
             ev[k][1].record(stream)
@@ -435,61 +413,52 @@ def run_batched(args, world, rank, local):
         return sum(a.elapsed_time(c) for a, c in ev) / 1e3
 
     l0 = b.launches()
-    with ClockSampler(local) as clk:
+    with ClockSampler(dev.index) as clk:
         t_persist = timed(b.step)
-    launches = b.launches() - l0 - 2 * args.warmup
-    t_loop = timed(b.step_looped)
+    launches = b.launches() - l0 - 2 * warmup
+    with ClockSampler(dev.index) as clk_loop:
+        t_loop = timed(b.step_looped)
     b.sync()
-    t_max = _max_over_ranks(t_persist, world)
-    value = cells * 2 * args.steps * world / t_max
-
     # end to end through the C ABI with host buffers, every run, every step
     hosts = [torch.from_numpy(w["U"]).pin_memory() for w in ws]
     outs = [torch.empty_like(h).pin_memory() for h in hosts]
+    ne = max(2, steps // 4)
     torch.cuda.synchronize()
     e0 = time.perf_counter()
-    for _ in range(args.steps):
+    for _ in range(ne):
         for i in range(len(ws)):
             rsst.rsst_batch_set_state(b.b, i, hosts[i], on_host=True)
         b.step(1)
         for i in range(len(ws)):
             rsst.rsst_batch_get_state(b.b, i, outs[i], on_host=True)
     torch.cuda.synchronize()
-    e_el = _max_over_ranks(time.perf_counter() - e0, world)
+    e_el = time.perf_counter() - e0
     nbytes = sum(h.numel() * 8 for h in hosts)
     b.close()
-    if rank != 0:
-        return
-    peaks, src = _peaks()
-    launch_s = t_persist / (2 * args.steps)
-    hbm = 40 * cells / launch_s / 1e9
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": t_max / args.steps * 1e3, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32 (perturbation about an f64 background)",
-            "data": "synthetic",
-            "config": {"workload": "batched: 64 independent 2D shear layers, N in {128..1024}^2, xi in {1,3,10,30}, "
-                                   "density ratio in {1,3,10,100}, FP32 perturbation, PVS, adaptive CFL per run",
-                       "cells": cells, "tile_shape": shape, "autotune_choice": choice,
-                       "l2": "inputs larger than L2 (0.64 GB of state)", "parallelism": f"replicas x{args.gpus}"},
+    launch_s = t_persist / (2 * steps)
+    alg = 40 * cells
+    hbm = alg / launch_s / 1e9
+    return {"value": cells * 2 * steps / t_persist, "unit": UNIT, "steps": steps, "warmup": warmup,
+            "ms_per_step": t_persist / steps * 1e3, "cells": cells, "runs": len(ws),
+            "tile_shape": shape, "autotune_choice": choice, "autotune_ms_per_step": tune_ms,
             "roofline": {"bound": "hbm", "achieved": hbm, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                          "frac": hbm / peaks["hbm_gbs"], "traffic": _traffic_key(f"batched:fp32_pert:{len(ws)}"),
-                         "peak_source": src},
-            "looped_single_run": {"value": cells * 2 * args.steps / t_loop, "ms_per_step": t_loop / args.steps * 1e3},
-            "e2e": {"value": cells * 2 * args.steps * world / e_el, "unit": UNIT,
+                         "algorithmic_bytes_per_launch": alg, "peak_source": src},
+            "looped_single_run": {"value": cells * 2 * steps / t_loop, "ms_per_step": t_loop / steps * 1e3,
+                                  "clocks": clk_loop.summary()},
+            "persistent_over_looped": t_loop / t_persist,
+            "e2e": {"value": cells * 2 * ne / e_el, "unit": UNIT, "steps": ne,
                     "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
-            "gpu_launches": launches, "clocks": clk.summary()}
-    print(json.dumps(line), flush=True)
+            "gpu_launches": launches, "clocks": clk.summary(), "l2": "inputs larger than L2 (0.8 GB of state)"}
 
 
-def run_adjoint(args, world, rank, local):
+def measure_adjoint(dev, steps=3, warmup=1):
     """Discrete adjoint of the 2D 256^2 float64 stratified box (contrast 20,
     xi = 20): forward record of 400 steps with a checkpoint every 20, then the
-    reverse sweep for dJ/dU0 and dJ/dxi of the final kinetic energy.  One
-    bench step is one such full gradient; the value counts the primal
-    cell-stages (cells x 2 x 400) per second of forward + reverse."""
+    reverse sweep for dJ/dU0 and dJ/dxi of the final kinetic energy; one
+    bench step is one full gradient, timed with CUDA events.  The value counts
+    the primal cell-stages (cells x 2 x 400) per second of forward + reverse."""
     from paper_1812_04135_gb300 import inputs, rsst
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
     w = inputs.polytrope_2d(256, 256, xi=20.0, contrast=20.0, amp=1e-3)
     cells, nsteps, every = 256 * 256, 400, 20
     stream = torch.cuda.current_stream(dev)
@@ -508,55 +477,141 @@ def run_adjoint(args, world, rank, local):
             dxi += rsst.rsst_adjoint_step(s.h, seg, g)
         return dxi
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         gradient(U0)
     torch.cuda.synchronize()
     l0 = s.launches()
-    _barrier(world)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with ClockSampler(local) as clk:
-        e0.record(stream)
-        for _ in range(args.steps):
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    with ClockSampler(dev.index) as clk:
+        for k in range(steps):
+            ev[k][0].record(stream)
             dxi = gradient(U0)
-        e1.record(stream)
+            ev[k][1].record(stream)
         torch.cuda.synchronize()
-    _barrier(world)
     launches = s.launches() - l0
-    t_max = _max_over_ranks(e0.elapsed_time(e1) / 1e3, world)
-    value = cells * 2 * nsteps * args.steps * world / t_max
-    # end to end: the initial state from pinned host memory, the gradient back to it
+    t = sum(a.elapsed_time(b) for a, b in ev) / 1e3
     host_in = torch.from_numpy(w["U"]).pin_memory()
     host_out = torch.empty_like(host_in).pin_memory()
     torch.cuda.synchronize()
     w0 = time.perf_counter()
-    for _ in range(args.steps):
+    for _ in range(steps):
         gradient(host_in, on_host=True)
         host_out.copy_(g, non_blocking=True)
         torch.cuda.synchronize()
-    e_el = _max_over_ranks(time.perf_counter() - w0, world)
+    e_el = time.perf_counter() - w0
     s.close()
+    primal = cells * 2 * nsteps
+    launch_s = t / steps  # one gradient
+    roof = _roof_alu(ADJ_FLOPS_PER_CELL_STAGE_2D, primal, launch_s, dev,
+                     "algorithmic float64 operations per primal cell-stage of forward record, segment recompute "
+                     "and reverse sweep (bench.py ADJ_FLOPS_PER_CELL_STAGE_2D); whole gradient, all kernels")
+    return {"value": primal * steps / t, "unit": UNIT + " (primal cell-stages of forward record + reverse sweep)",
+            "steps": steps, "warmup": warmup, "ms_per_step": t / steps * 1e3, "cells": cells,
+            "steps_per_gradient": nsteps, "checkpoint_every": every, "roofline": roof, "clocks": clk.summary(),
+            "gpu_launches": launches, "dJ_dxi": dxi,
+            "e2e": {"value": primal * steps / e_el, "unit": UNIT, "steps": steps,
+                    "h2d_bytes_per_step": host_in.numel() * 8, "d2h_bytes_per_step": host_out.numel() * 8}}
+
+
+def run_modes(dev, peaks, src):
+    """The other configurations the metric covers, each as a full entry
+    (CUDA events, clocks, roofline, e2e), for the same JSON line."""
+    from paper_1812_04135_gb300 import inputs, rsst
+    out = {}
+    hbm_fp32 = "hbm (instruction-issue limited)"
+    w = inputs.shear_layer_2d(512, 512, xi=30.0, variant="pvs")
+    out["fp32_pert_shear_512"] = measure_single(w, "fp32_pert", 20, 3, dev, peaks, src, bound=hbm_fp32,
+                                                traffic_key="shear2d:fp32_pert:512")
+    w = inputs.shear_layer_2d(2048, 2048, xi=30.0, variant="pvs")
+    out["fp32_pert_shear_2048"] = measure_single(w, "fp32_pert", 20, 3, dev, peaks, src, flush_l2=False,
+                                                 bound=hbm_fp32, traffic_key="shear2d:fp32_pert:2048", e2e_steps=5)
+    w = inputs.shear_layer_2d(4096, 4096, xi=30.0, variant="pvs")
+    out["fp32_pert_shear_4096"] = measure_single(w, "fp32_pert", 20, 3, dev, peaks, src, flush_l2=False,
+                                                 bound=hbm_fp32, traffic_key="shear2d:fp32_pert:4096", e2e_steps=3)
+    out["fp64_shear_4096"] = measure_single(w, "fp64", 20, 3, dev, peaks, src, flush_l2=False,
+                                            traffic_key="shear2d:fp64:4096", e2e_steps=3,
+                                            alu_flops=(FP64_FLOPS_PER_CELL_STAGE_2D, FP64_FLOP_COUNT))
+    del w
+    w = inputs.polytrope_3d(variant="pvs")
+    out["fp64_polytrope_3d"] = measure_single(w, "fp64", 20, 3, dev, peaks, src, flush_l2=False,
+                                              traffic_key="polytrope3d:fp64:256", e2e_steps=5,
+                                              bound="alu (float64 pipe); HBM roofline of the primary 3D configuration")
+    out["fp32_pert_polytrope_3d"] = measure_single(w, "fp32_pert", 20, 3, dev, peaks, src, flush_l2=False,
+                                                   bound=hbm_fp32, traffic_key="polytrope3d:fp32_pert:256",
+                                                   e2e_steps=5)
+    df = {"dtype": "f32x2 double-float (48-bit significand), parity 1e-10 vs f64"}
+    out["fp64_df_polytrope_3d"] = measure_single(w, "fp64_df", 10, 2, dev, peaks, src, flush_l2=False,
+                                                 bound="alu (float32 pipe, double-float arithmetic)", extra=df,
+                                                 e2e_steps=2)
+    w = inputs.shear_layer_2d(512, 512, xi=30.0, variant="pvs")
+    out["fp64_df_shear_512"] = measure_single(w, "fp64_df", 20, 3, dev, peaks, src,
+                                              bound="alu (float32 pipe, double-float arithmetic)", extra=df)
+    del w
+    out["batched_fp32_pert_64runs"] = measure_batched(dev, peaks, src)
+    out["adjoint_fp64_polytrope_256"] = measure_adjoint(dev)
+    # 1D N=256 sound wave, 2000 steps: launch-bound; CUDA-graph blocks vs plain launches
+    w = inputs.sound_wave_1d(256, xi=10.0, variant="pvs")
+    for k, name in ((16, "fp64_sound1d_256_graph"), (0, "fp64_sound1d_256_plain")):
+        stream = torch.cuda.current_stream(dev)
+        s = rsst.Solver(w, "fp64", stream=stream)
+        s.set_graph_steps(k)
+        s.set_state(torch.from_numpy(w["U"]).to(dev))
+        s.step(64)
+        s.sync()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with ClockSampler(dev.index) as clk:
+            e0.record(stream)
+            s.step(2000)
+            e1.record(stream)
+            torch.cuda.synchronize()
+        s.sync()
+        s.close()
+        t = e0.elapsed_time(e1) / 1e3
+        out[name] = {"value": 256 * 2 * 2000 / t, "unit": UNIT, "steps_per_s": 2000 / t, "steps": 2000,
+                     "graph_steps": k, "bound": "launch latency", "clocks": clk.summary()}
+    return out
+
+
+def run_batched(args, world, rank, local):
+    """The batched workload as the bench's main line (--workload batched)."""
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    peaks, src = _peaks()
+    d = measure_batched(dev, peaks, src, steps=args.steps, warmup=args.warmup, world=world)
+    t_max = _max_over_ranks(d["ms_per_step"] * args.steps / 1e3, world)
     if rank != 0:
         return
-    c = clk.summary()
-    sm_mhz = c["sm_mhz"] or 1900.0
-    flops = ADJ_FLOPS_PER_CELL_STAGE_2D * cells * 2 * nsteps * args.steps / t_max
-    peak_tf = fp64_peak_tflops(sm_mhz)
-    line = {"metric": METRIC, "value": value, "unit": UNIT + " (primal cell-stages of forward record + reverse sweep)",
-            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": t_max / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+    line = {"metric": METRIC, "value": d["cells"] * 2 * args.steps * world / t_max, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 (perturbation about an f64 background)", "data": "synthetic",
+            "config": {"workload": "batched: 64 independent 2D shear layers, N in {128..1024}^2, xi in {1,3,10,30}, "
+                                   "density ratio in {1,3,10,100}, FP32 perturbation, PVS, adaptive CFL per run",
+                       "cells": d["cells"], "tile_shape": d["tile_shape"], "autotune_choice": d["autotune_choice"],
+                       "l2": d["l2"], "parallelism": f"replicas x{args.gpus}"},
+            "roofline": d["roofline"], "looped_single_run": d["looped_single_run"],
+            "e2e": d["e2e"], "gpu_launches": d["gpu_launches"], "clocks": d["clocks"]}
+    print(json.dumps(line), flush=True)
+
+
+def run_adjoint(args, world, rank, local):
+    """The adjoint workload as the bench's main line (--workload adjoint)."""
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    d = measure_adjoint(dev, steps=args.steps, warmup=args.warmup)
+    t_max = _max_over_ranks(d["ms_per_step"] * args.steps / 1e3, world)
+    if rank != 0:
+        return
+    line = {"metric": METRIC, "value": d["cells"] * 2 * 400 * args.steps * world / t_max, "unit": d["unit"],
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": "adjoint: 2D 256x256 stratified box, contrast 20, xi=20, FP64 PVS, 400 steps, "
                                    "checkpoint every 20, gradient of the final kinetic energy w.r.t. U0 and xi",
-                       "cells": cells, "steps_per_gradient": nsteps, "checkpoint_every": every,
+                       "cells": d["cells"], "steps_per_gradient": 400, "checkpoint_every": 20,
                        "l2": "working set (checkpoints, recompute storage) larger than L2",
                        "parallelism": f"replicas x{args.gpus}"},
-            "roofline": {"bound": "alu", "achieved": flops / 1e12, "peak": peak_tf, "unit": "TFLOP/s",
-                         "frac": flops / 1e12 / peak_tf, "traffic": None,
-                         "scope": "whole gradient (forward, recompute and VJP kernels), algorithmic float64 count",
-                         "peak_source": f"float64: 152 SMs x 2 DFMA/clk x 2 flop x {sm_mhz:.0f} MHz"},
-            "e2e": {"value": cells * 2 * nsteps * args.steps * world / e_el, "unit": UNIT,
-                    "h2d_bytes_per_step": host_in.numel() * 8, "d2h_bytes_per_step": host_out.numel() * 8},
-            "gpu_launches": launches, "clocks": c, "dJ_dxi": dxi}
+            "roofline": d["roofline"], "e2e": d["e2e"], "gpu_launches": d["gpu_launches"], "clocks": d["clocks"],
+            "dJ_dxi": d["dJ_dxi"]}
     print(json.dumps(line), flush=True)
 
 
@@ -749,26 +804,17 @@ def run_gpu(args, world, rank, local):
     nbytes = host_in.numel() * 8
     s.close()
 
-    if rank != 0:
-        return
     peaks, src = _peaks()
     c = clk.summary()
-    sm_mhz = c["sm_mhz"] or peaks.get("clocks_under_load", {}).get("sm_mhz_median", 1900.0)
     launch_s = t_dev / (2 * args.steps)
-    alg_bytes = bytes_per_cell_stage(w, args.precision) * cells
-    hbm_gbs = alg_bytes / launch_s / 1e9
+    hbm = _roof_hbm(w, args.precision, cells, launch_s, peaks, src, f"{args.workload}:{args.precision}:{w['n'][0]}")
     if args.precision == "fp64" and w["ndim"] == 2:
-        flops = FP64_FLOPS_PER_CELL_STAGE_2D * cells
-        peak_tf = fp64_peak_tflops(sm_mhz)
-        achieved_tf = flops / launch_s / 1e12
-        roof = {"bound": "alu", "achieved": achieved_tf, "peak": peak_tf, "unit": "TFLOP/s",
-                "frac": achieved_tf / peak_tf, "traffic": None,
-                "peak_source": f"float64: 152 SMs x 2 DFMA/clk x 2 flop x {sm_mhz:.0f} MHz (unit count measured)",
-                "hbm_achieved_gbs": hbm_gbs, "hbm_peak_gbs": peaks["hbm_gbs"],
-                "hbm_frac": hbm_gbs / peaks["hbm_gbs"], "hbm_peak_source": src}
+        roof = _roof_alu(FP64_FLOPS_PER_CELL_STAGE_2D, cells, launch_s, dev, FP64_FLOP_COUNT)
+        roof["hbm"] = {k: hbm[k] for k in ("achieved", "peak", "frac", "traffic", "unit")}
     else:
-        roof = {"bound": "hbm", "achieved": hbm_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": hbm_gbs / peaks["hbm_gbs"], "traffic": None, "peak_source": src}
+        roof = hbm
+    if rank != 0:
+        return
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_max / args.steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
@@ -779,11 +825,8 @@ def run_gpu(args, world, rank, local):
             "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
             "gpu_launches": launches, "clocks": c, "wall_s": wall,
             "step_ms_min": min(step_ms), "step_ms_median": statistics.median(step_ms)}
-    trf = _traffic_for(args, w)
-    if trf is not None:
-        line["roofline"]["traffic"] = trf
     if world == 1 and not args.no_modes and args.workload == "shear2d" and args.precision == "fp64" and args.n == 512:
-        line["modes"] = run_modes(dev, peaks, sm_mhz)
+        line["modes"] = run_modes(dev, peaks, src)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w, args.cpu_seconds)
     print(json.dumps(line), flush=True)

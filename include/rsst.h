@@ -359,6 +359,14 @@ int64_t rsst_kernel_launches(const rsst_handle* h);
  * Synchronous, current device. */
 int rsst_math_selftest(int32_t n, double* rcp_max_ulp, int32_t* mc_mismatches, double* sqrt_max_rel);
 
+/* Float64 FMA throughput of the current device in TFLOP/s, measured by a
+ * probe kernel (independent FMA chains on every SM, timed with CUDA events
+ * after a warm-up launch; `iters` x 32 FMAs per thread), and the launch time
+ * in ms (ms may be NULL).  The denominator of the float64 step's arithmetic
+ * roofline: a performance measurement with no counterpart in the paper.
+ * Synchronous, current device. */
+int rsst_fp64_fma_peak(int32_t iters, double* tflops, double* ms);
+
 /* sizeof(rsst_config) as compiled into the library (binding check; no
  * counterpart in the paper). */
 size_t rsst_config_size(void);

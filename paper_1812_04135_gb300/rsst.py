@@ -67,6 +67,7 @@ def lib():
             "rsst_conserved_sums_noalloc": (i32, [vp, i32, C.POINTER(C.c_int32), pd, vp, vp]),
             "rsst_config_size": (C.c_size_t, []),
             "rsst_math_selftest": (i32, [i32, pd, C.POINTER(C.c_int32), pd]),
+            "rsst_fp64_fma_peak": (i32, [i32, pd, pd]),
             "rsst_adjoint_record": (i32, [vp, dbl, i32, i32]),
             "rsst_adjoint_segments": (i32, [vp, C.POINTER(C.c_int32)]),
             "rsst_adjoint_step": (i32, [vp, i32, vp, pd]),
@@ -278,6 +279,13 @@ def rsst_math_selftest(n: int = 1 << 20):
     rel = C.c_double()
     _check(lib().rsst_math_selftest(int(n), C.byref(ulp), C.byref(bad), C.byref(rel)), "rsst_math_selftest")
     return ulp.value, bad.value, rel.value
+
+
+def rsst_fp64_fma_peak(iters: int = 20000):
+    """Measured float64 FMA throughput (TFLOP/s, launch ms) of the current device."""
+    tf, ms = C.c_double(), C.c_double()
+    _check(lib().rsst_fp64_fma_peak(int(iters), C.byref(tf), C.byref(ms)), "rsst_fp64_fma_peak")
+    return tf.value, ms.value
 
 
 def rsst_set_graph_steps(h: int, k: int) -> None:

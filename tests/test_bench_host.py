@@ -1,8 +1,8 @@
 """Host-side logic of bench.py that its numbers rest on (no GPU): the stored
 DRAM traffic is used only while the kernel sources it was measured on are
 unchanged (comments aside), the algorithmic bytes per cell-stage, the
-float64 peak from unit counts and clock, and the clock-record parsing that
-decides whether a run is kept."""
+roofline arithmetic, and the clock-record parsing that decides whether a
+run is kept."""
 import json
 
 import pytest
@@ -46,9 +46,16 @@ def test_algorithmic_bytes_per_cell_stage():
     assert bench.bytes_per_cell_stage({"ndim": 1}, "fp64_df") == 60.0
 
 
-def test_float64_peak_from_unit_counts():
-    # 152 SMs x 2 DFMA per clock x 2 flops x 2.07 GHz
-    assert bench.fp64_peak_tflops(2070.0) == pytest.approx(1.25856, rel=1e-12)
+def test_roofline_objects(monkeypatch):
+    """achieved = algorithmic bytes (or flops) per launch / launch time; frac
+    = achieved / peak; the float64 peak is the measured probe's."""
+    monkeypatch.setattr(bench, "fp64_peak_measured", lambda dev: (1.2, 300.0, 2070.0))
+    peaks = {"hbm_gbs": 6000.0}
+    h = bench._roof_hbm({"ndim": 2}, "fp32_pert", 1000, 1e-6, peaks, "measured", None)
+    assert h["achieved"] == pytest.approx(40 * 1000 / 1e-6 / 1e9) and h["frac"] == pytest.approx(h["achieved"] / 6000.0)
+    a = bench._roof_alu(309, 1000, 1e-6, None, "count")
+    assert a["achieved"] == pytest.approx(309 * 1000 / 1e-6 / 1e12) and a["peak"] == 1.2
+    assert a["frac"] == pytest.approx(a["achieved"] / 1.2)
 
 
 def test_clock_record_from_nvidia_smi_lines():

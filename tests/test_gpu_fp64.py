@@ -197,6 +197,13 @@ def test_float64_helpers_against_cuda():
     assert rel <= 2.0 ** -40, rel
 
 
+def test_fp64_fma_peak_probe():
+    """The float64 throughput probe behind the arithmetic roofline returns a
+    plausible rate (GB300: about 1.2 TFLOP/s)."""
+    tf, ms = rsst.rsst_fp64_fma_peak(2000)
+    assert 0.2 < tf < 5.0 and ms > 0.0, (tf, ms)
+
+
 @pytest.mark.parametrize("ndim", [1, 2, 3])
 def test_cmax_law(ndim):
     """State-dependent xi = [1 + (a/C_max)^4]^(1/4) (Eq. cx) in c_tot and f."""
