@@ -102,7 +102,7 @@ typedef struct rsst_config {
   int32_t variant;     /* rsst_variant */
   int32_t precision;   /* rsst_precision */
   double xi;           /* reduction rate, >= 1 (constant, Sec. 4.3) */
-  double gamma;        /* ratio of specific heats (ideal gas) */
+  double gamma;        /* ratio of specific heats */
   double cfl;          /* Courant number (0.4 in Sec. 4.2) */
   double grav[3];      /* constant acceleration F of App. B */
   int32_t vertical;    /* background axis, or -1 */
@@ -115,6 +115,13 @@ typedef struct rsst_config {
   double cmax;         /* > 0: state-dependent reduction xi = [1 + (a/cmax)^4]^(1/4)
                         * (Eq. cx, Sec. 4.3) in c_tot and in f = 1 - 1/xi^2, per
                         * face state and per cell; 0: the constant xi above */
+  double covolume;     /* equation of state (Sec. 3.2 states the reduced equations
+                        * and dP for any EOS): 0 is the ideal gas; b > 0 the
+                        * covolume (Noble-Abel) gas P = (gamma-1) e / (1 - b rho),
+                        * a^2 = gamma P / (rho (1 - b rho)), e the internal energy
+                        * per volume.  RSST_FP64 runs only (RSST_EUNSUPPORTED
+                        * otherwise, and for the adjoint); a state with b rho >= 1
+                        * is non-physical. */
 } rsst_config;
 
 typedef struct rsst_handle rsst_handle;
@@ -124,8 +131,10 @@ typedef struct rsst_handle rsst_handle;
  * the current CUDA device; *h is NULL on failure and everything allocated is
  * freed.  `stream` is a cudaStream_t (may be NULL).  Errors: RSST_EINVAL for
  * an invalid config, checked before any device call (ndim, n, dx, bc, form,
- * precision, xi >= 1, gamma > 1, cfl > 0, cfl_rule 0 or 1, cmax >= 0, finite gravity, the
- * background entries); RSST_ENOMEM when an allocation fails; RSST_ECUDA
+ * precision, xi >= 1, gamma > 1, cfl > 0, cfl_rule 0 or 1, cmax >= 0,
+ * covolume >= 0, finite gravity, the background entries, with b rho0 < 1);
+ * RSST_EUNSUPPORTED for covolume > 0 in a precision other than RSST_FP64
+ * (also checked first); RSST_ENOMEM when an allocation fails; RSST_ECUDA
  * when a copy, kernel or tensor-map encoding fails.  Synchronous. */
 int rsst_init(rsst_handle** h, const rsst_config* cfg, void* stream);
 
@@ -214,7 +223,8 @@ int rsst_conserved_sums(rsst_handle* h, double* sums);
  * allocated here (library-owned): ceil(nsteps/every) checkpoints, 2 x every
  * recompute states and their Euler tendencies, and a few state-sized work
  * arrays; RSST_ENOMEM if that fails.  The handle ends at U^{nsteps}.
- * RSST_EUNSUPPORTED for runs that are not float64.  Asynchronous. */
+ * RSST_EUNSUPPORTED for runs that are not float64 or not the ideal gas
+ * (covolume > 0).  Asynchronous. */
 int rsst_adjoint_record(rsst_handle* h, double dt, int nsteps, int every);
 
 /* Number of recorded segments, ceil(nsteps / every) (no counterpart in the

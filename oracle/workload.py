@@ -7,6 +7,7 @@ from dataclasses import replace
 import torch
 
 from . import rsst_oracle as ro
+from .eos import NobleAbel
 
 VARIANTS = {"euler": ro.EULER, "dvs": ro.DVS, "pvs": ro.PVS, "dms": ro.DMS, "pms": ro.PMS, "pd": ro.PD}
 BCS = {"periodic": ro.PERIODIC, "reflect": ro.REFLECT}
@@ -15,7 +16,8 @@ BCS = {"periodic": ro.PERIODIC, "reflect": ro.REFLECT}
 def problem_from(w: dict, **over):
     v = w["variant"]
     prob = ro.Problem(
-        ndim=w["ndim"], n=tuple(w["n"]), dx=tuple(w["dx"]), gamma=w["gamma"], xi=w["xi"],
+        ndim=w["ndim"], n=tuple(w["n"]), dx=tuple(w["dx"]),
+        gamma=NobleAbel(w["gamma"], w["covolume"]) if w.get("covolume") else w["gamma"], xi=w["xi"],
         variant=VARIANTS[v] if isinstance(v, str) else int(v),
         grav=tuple(w["grav"]), bc=tuple(BCS[b] for b in w["bc"]), cfl=w.get("cfl", 0.4),
         vertical=w["vertical"],

@@ -619,6 +619,10 @@ extern "C" int rsst_adjoint_record(rsst_handle* h, double dt, int nsteps, int ev
     rsst_set_error("rsst_adjoint_record: the adjoint is float64 only");
     return RSST_EUNSUPPORTED;
   }
+  if (h->cfg.covolume != 0.0) {
+    rsst_set_error("rsst_adjoint_record: the adjoint is derived for the ideal gas only");
+    return RSST_EUNSUPPORTED;
+  }
   rsst_adjoint_free(h);
   AdjState* s = new AdjState();
   h->adj = s;

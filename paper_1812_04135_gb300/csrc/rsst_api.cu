@@ -117,6 +117,10 @@ static int make_tmap_2d(CUtensorMap* m, void* base, const Geom& g, int nv, int b
 
 static int validate(const rsst_config* c) {
   if (!c) { rsst_set_error("config is NULL"); return RSST_EINVAL; }
+  if (c->covolume != 0.0 && c->precision != RSST_FP64) {
+    rsst_set_error("a covolume gas is implemented in the RSST_FP64 precision only");
+    return RSST_EUNSUPPORTED;
+  }
   if (c->ndim < 1 || c->ndim > 3) { rsst_set_error("ndim must be 1, 2 or 3 (got %d)", c->ndim); return RSST_EINVAL; }
   for (int d = 0; d < c->ndim; ++d) {
     if (c->n[d] < 2) { rsst_set_error("n[%d] must be >= 2 (got %d)", d, c->n[d]); return RSST_EINVAL; }
@@ -132,6 +136,10 @@ static int validate(const rsst_config* c) {
   for (int d = 0; d < c->ndim; ++d)
     if (!std::isfinite(c->grav[d])) { rsst_set_error("grav[%d] must be finite", d); return RSST_EINVAL; }
   if (!(c->cmax >= 0.0) || !std::isfinite(c->cmax)) { rsst_set_error("cmax must be >= 0 (0: constant xi)"); return RSST_EINVAL; }
+  if (!(c->covolume >= 0.0) || !std::isfinite(c->covolume)) {
+    rsst_set_error("covolume must be finite and >= 0 (0: ideal gas)");
+    return RSST_EINVAL;
+  }
   if (c->vertical < -1 || c->vertical >= c->ndim) { rsst_set_error("vertical axis %d invalid", c->vertical); return RSST_EINVAL; }
   if (c->vertical >= 0 && (!c->bg_rho || !c->bg_p)) { rsst_set_error("background profiles required when vertical >= 0"); return RSST_EINVAL; }
   if (c->vertical >= 0) {
@@ -139,8 +147,9 @@ static int validate(const rsst_config* c) {
     const int nvert = c->n[c->vertical];
     const bool wrap = c->bc[c->vertical] == RSST_BC_PERIODIC;
     for (int k = wrap ? RSST_G : 0; k < (wrap ? nvert + RSST_G : nvert + 2 * RSST_G); ++k)
-      if (!(c->bg_rho[k] > 0.0) || !(c->bg_p[k] > 0.0) || !std::isfinite(c->bg_rho[k]) || !std::isfinite(c->bg_p[k])) {
-        rsst_set_error("background entry %d must be finite with rho > 0 and P > 0", k);
+      if (!(c->bg_rho[k] > 0.0) || !(c->bg_p[k] > 0.0) || !std::isfinite(c->bg_rho[k]) || !std::isfinite(c->bg_p[k]) ||
+          !(c->covolume * c->bg_rho[k] < 1.0)) {
+        rsst_set_error("background entry %d must be finite with rho > 0, P > 0 and covolume * rho < 1", k);
         return RSST_EINVAL;
       }
   }
@@ -197,6 +206,7 @@ static void make_phys(const rsst_config* c, Phys* p) {
   p->use_cmax = c->cmax > 0.0;
   p->inv_cmax4 = p->use_cmax ? 1.0 / (c->cmax * c->cmax * c->cmax * c->cmax) : 0.0;
   p->cfl = c->cfl;
+  p->covol = c->covolume;
   p->variant = c->variant;
   p->vertical = c->vertical;
   p->sum_inv_dx = 0.0;
@@ -288,7 +298,10 @@ extern "C" int rsst_init(rsst_handle** out, const rsst_config* cfg, void* stream
       int src = k;
       if (cfg->bc[cfg->vertical] == RSST_BC_PERIODIC) src = ((k - RSST_G) % nvert + nvert) % nvert + RSST_G;
       tmp[k] = cfg->bg_rho[src];
-      tmp[h->bg_len + k] = cfg->bg_p[src] / (cfg->gamma - 1.0);
+      // E0 = e(rho0, P0): P0/(gamma-1), times (1 - b rho0) for a covolume gas
+      tmp[h->bg_len + k] = cfg->covolume == 0.0 ? cfg->bg_p[src] / (cfg->gamma - 1.0)
+                                                : cfg->bg_p[src] * (1.0 - cfg->covolume * cfg->bg_rho[src]) /
+                                                      (cfg->gamma - 1.0);
     }
     ALLOC(h->d_bg, 2 * h->bg_len * sizeof(double));
     const cudaError_t e = cudaMemcpy(h->d_bg, tmp, 2 * h->bg_len * sizeof(double), cudaMemcpyHostToDevice);

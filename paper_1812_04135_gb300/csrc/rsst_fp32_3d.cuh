@@ -5,10 +5,12 @@
 // all five fields; x origin rounded down to a 16-byte boundary) stream
 // through an NS = 5 slot shared-memory ring, one cp.async.bulk.tensor per
 // plane issued three planes ahead, each slot with its own mbarrier (bounded
-// waits).  Per plane k, with three block barriers:
+// waits).  Per plane k, with two block barriers:
 //   A. every thread takes the y half slope of its cell, writes the cell's
 //      upper y face state U + h to shared memory and keeps the lower one;
-//      the first and last warps also take the halo rows -1 and BY;
+//      the first and last warps also take the halo rows -1 and BY (done at
+//      the end of step C of the previous plane, so the barrier that opens
+//      the plane also publishes these states);
 //   B. every thread forms twice the LLF flux of the y face below its cell
 //      from the state written by the cell below (the last warp also the
 //      face above the block), and the warps walk the x faces of the plane in chunks of 32
@@ -174,6 +176,40 @@ __global__ void __launch_bounds__(T3::NT, 5) stage3d_tma_kernel(const __grid_con
 #pragma unroll
     for (int v = 0; v < NV; ++v) bnext[v] = a.base[v * fs + o0];
   }
+  // A. y half slope of my cell in plane pl (value u): its upper face state
+  // to shared memory, its lower one kept in qBot; the first warp also writes
+  // row -1's upper state, the last warp keeps row BY's lower state in qBotN.
+  // Done for plane k at the end of step C of plane k-1 (the exchange array is
+  // free once step B has read it), so a plane takes two block barriers.
+  float qBot[NV], qBotN[NV];
+  auto ystates = [&](int pl, const float (&u)[NV]) {
+    const float* Pc = ring + slot_of(pl) * T3::PLANE + sxy;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      const float um = Pc[v * T3::PF - T3::SXP], up = Pc[v * T3::PF + T3::SXP];
+      const float h = half_mc_f(u[v] - um, up - u[v]);
+      sQ[(v * T3::QROWS + cy + 1) * T3::BX + cx] = u[v] + h;
+      qBot[v] = u[v] - h;
+    }
+    if (cy == 0) {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        const float* c = Pc + v * T3::PF - T3::SXP;  // row -1
+        const float um = c[-T3::SXP], uu = c[0], up = c[T3::SXP];
+        sQ[(v * T3::QROWS + 0) * T3::BX + cx] = uu + half_mc_f(uu - um, up - uu);
+      }
+    }
+    if (cy == T3::BY - 1) {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        const float* c = Pc + v * T3::PF + T3::SXP;  // row BY
+        const float um = c[-T3::SXP], uu = c[0], up = c[T3::SXP];
+        qBotN[v] = uu - half_mc_f(uu - um, up - uu);
+      }
+    }
+  };
+  ystates(k0, u0);
+
 #pragma unroll 1
   for (int k = k0; k < k1; ++k) {
     // everyone sees plane k+2 and the slot of plane k-2 is free
@@ -192,35 +228,6 @@ __global__ void __launch_bounds__(T3::NT, 5) stage3d_tma_kernel(const __grid_con
     const float* P = ring + slot_of(k) * T3::PLANE;
     float4 cb = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     if constexpr (BG) cb = *reinterpret_cast<const float4*>(st + rz * TR_W + TR_RHO0);
-    // A. y half slope of my cell: its upper face state to shared memory, its
-    // lower one kept; the first warp also writes row -1's upper state, the
-    // last warp keeps row BY's lower state
-    const float* Pc = P + sxy;
-    float qBot[NV], qBotN[NV];
-#pragma unroll
-    for (int v = 0; v < NV; ++v) {
-      const float um = Pc[v * T3::PF - T3::SXP], up = Pc[v * T3::PF + T3::SXP];
-      const float h = half_mc_f(u0[v] - um, up - u0[v]);
-      sQ[(v * T3::QROWS + cy + 1) * T3::BX + cx] = u0[v] + h;
-      qBot[v] = u0[v] - h;
-    }
-    if (cy == 0) {
-#pragma unroll
-      for (int v = 0; v < NV; ++v) {
-        const float* c = Pc + v * T3::PF - T3::SXP;  // row -1
-        const float um = c[-T3::SXP], u = c[0], up = c[T3::SXP];
-        sQ[(v * T3::QROWS + 0) * T3::BX + cx] = u + half_mc_f(u - um, up - u);
-      }
-    }
-    if (cy == T3::BY - 1) {
-#pragma unroll
-      for (int v = 0; v < NV; ++v) {
-        const float* c = Pc + v * T3::PF + T3::SXP;  // row BY
-        const float um = c[-T3::SXP], u = c[0], up = c[T3::SXP];
-        qBotN[v] = u - half_mc_f(u - um, up - u);
-      }
-    }
-    __syncthreads();
     // B. y faces, then the x faces of the plane
     {
       float qL[NV], G[NV];
@@ -329,6 +336,7 @@ __global__ void __launch_bounds__(T3::NT, 5) stage3d_tma_kernel(const __grid_con
       h0[v] = h1[v];
       Fm[v] = Fp[v];
     }
+    if (k + 1 < k1) ystates(k + 1, u0);  // step A of the next plane (resident: plane k+2 was waited for)
   }
   if (ST == 2) {
     if (!ok_all) atomicOr(a.flag, RSST_FLAG_NONPHYSICAL);

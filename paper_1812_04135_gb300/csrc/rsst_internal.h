@@ -42,6 +42,7 @@ struct Phys {
   double inv_cmax4;      // 1/C_max^4 (state-dependent xi, Eq. cx), used if use_cmax
   int use_cmax;
   double cfl;
+  double covol;          // covolume b of the gas (0: ideal gas)
   double grav[3];
   double inv_dx[3];
   double sum_inv_dx;     // sum_d 1/dx_d: CFL rate = c_tot * sum_inv_dx

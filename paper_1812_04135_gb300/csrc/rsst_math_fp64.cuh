@@ -8,32 +8,49 @@
 
 namespace rsst {
 
-// Equation-of-state hook (Sec. 3.2: the reduced equations hold for a general
+// Equation of state (Sec. 3.2: the reduced equations hold for a general
 // EOS; the pressure tendency needs (de/dP)_rho and (de/drho)_P, Eqs.
-// pvs_cons_dpr / pvs_cons_therm).  The float64 step reads its thermodynamics
-// only through these members; the library compiles the ideal gas
-// (e = P/(gamma-1), the only EOS the paper specifies).  Another EOS is a
-// struct with the same members selected by `Eos` below.
-struct IdealGasEos {
+// pvs_cons_dpr / pvs_cons_therm).  The float64 step reads its
+// thermodynamics only through these members.  Two gases: the ideal gas
+// (covolume b = 0, the only EOS the paper specifies), e = P/(gamma-1), and
+// the covolume (Noble-Abel) gas, P = (gamma-1) e / (1 - b rho),
+// a^2 = gamma P / (rho (1 - b rho)), (de/dP)_rho = (1 - b rho)/(gamma-1),
+// (de/drho)_P = -b P/(gamma-1).  The choice is uniform over a launch (a run's
+// b); with b = 0 every member is the ideal-gas expression unchanged.
+__device__ __forceinline__ double rcp_nr(double x);
+
+struct Eos {
+  // 1 - b rho, for b != 0
+  __device__ static __forceinline__ double omb(const Phys& p, double rho) { return fma(-p.covol, rho, 1.0); }
   // P from the total energy E and rho |V|^2
   __device__ static __forceinline__ double pressure(const Phys& p, double rho, double E, double rhov2) {
-    return p.gm1 * E - p.hgm1 * rhov2;
+    const double Pi = p.gm1 * E - p.hgm1 * rhov2;
+    return p.covol == 0.0 ? Pi : Pi * rcp_nr(omb(p, rho));
   }
   __device__ static __forceinline__ double sound2(const Phys& p, double rho, double P, double inv_rho) {
-    return p.gamma * P * inv_rho;
+    return p.covol == 0.0 ? p.gamma * P * inv_rho : p.gamma * P * inv_rho * rcp_nr(omb(p, rho));
   }
   // (a/xi)^2 for a constant xi, with gamma/xi^2 folded into one constant
   __device__ static __forceinline__ double sound2_over_xi2(const Phys& p, double rho, double P, double inv_rho) {
-    return p.gamma_xi2 * (P * inv_rho);
+    return p.covol == 0.0 ? p.gamma_xi2 * (P * inv_rho) : p.gamma_xi2 * (P * inv_rho) * rcp_nr(omb(p, rho));
   }
   __device__ static __forceinline__ double internal_energy(const Phys& p, double rho, double P) {
-    return P * p.inv_gm1;
+    return p.covol == 0.0 ? P * p.inv_gm1 : P * p.inv_gm1 * omb(p, rho);
   }
-  __device__ static __forceinline__ double de_dP(const Phys& p, double rho, double P) { return p.inv_gm1; }
-  __device__ static __forceinline__ double inv_de_dP(const Phys& p, double rho, double P) { return p.gm1; }
-  __device__ static __forceinline__ double de_drho(const Phys& p, double rho, double P) { return 0.0; }
+  __device__ static __forceinline__ double de_dP(const Phys& p, double rho, double P) {
+    return p.covol == 0.0 ? p.inv_gm1 : p.inv_gm1 * omb(p, rho);
+  }
+  __device__ static __forceinline__ double inv_de_dP(const Phys& p, double rho, double P) {
+    return p.covol == 0.0 ? p.gm1 : p.gm1 * rcp_nr(omb(p, rho));
+  }
+  __device__ static __forceinline__ double de_drho(const Phys& p, double rho, double P) {
+    return p.covol == 0.0 ? 0.0 : -p.covol * P * p.inv_gm1;
+  }
+  // a state the EOS admits: 1 - b rho > 0 (always true for the ideal gas)
+  __device__ static __forceinline__ bool admissible(const Phys& p, double rho) {
+    return p.covol == 0.0 || omb(p, rho) > 0.0;
+  }
 };
-using Eos = IdealGasEos;
 
 // 1/x to full float64 accuracy with three float64-pipe instructions: the
 // hardware reciprocal approximation y, then one third-order step of the
@@ -293,7 +310,7 @@ __device__ __forceinline__ double cfl_rate(const double (&q)[NV], const Phys& p,
     fin = fin && isfinite(q[1 + e]);
   }
   const double P = Eos::pressure(p, rho, q[NV - 1], rho * v2);
-  ok = fin && rho > 0.0 && P > 0.0;
+  ok = fin && rho > 0.0 && P > 0.0 && Eos::admissible(p, rho);
   const double c = sqrt_ctot(v2) + ctot_sound(p, rho, P, ir);
   return c * p.sum_inv_dx;
 }

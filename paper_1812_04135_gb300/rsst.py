@@ -35,6 +35,7 @@ class Config(C.Structure):
         ("variant", C.c_int32), ("precision", C.c_int32), ("xi", C.c_double), ("gamma", C.c_double),
         ("cfl", C.c_double), ("grav", C.c_double * 3), ("vertical", C.c_int32), ("cfl_rule", C.c_int32),
         ("bg_rho", C.POINTER(C.c_double)), ("bg_p", C.POINTER(C.c_double)), ("cmax", C.c_double),
+        ("covolume", C.c_double),
     ]
 
 
@@ -104,7 +105,7 @@ def _check(rc: int, where: str) -> int:
 
 def make_config(ndim, n, dx, *, variant="pvs", precision="fp64", xi=1.0, gamma=5.0 / 3.0, cfl=0.4,
                 grav=(0.0, 0.0, 0.0), bc=("periodic",) * 3, vertical=-1, bg_rho=None, bg_p=None, cmax=0.0,
-                cfl_rule=0):
+                cfl_rule=0, covolume=0.0):
     """Build an ``rsst_config``; the returned object keeps the background arrays alive."""
     cfg = Config()
     cfg.ndim = int(ndim)
@@ -120,6 +121,7 @@ def make_config(ndim, n, dx, *, variant="pvs", precision="fp64", xi=1.0, gamma=5
     cfg.vertical = int(vertical)
     cfg.cmax = float(cmax or 0.0)
     cfg.cfl_rule = int(cfl_rule)
+    cfg.covolume = float(covolume or 0.0)
     cfg._keep = []
     if bg_rho is not None:
         r = np.ascontiguousarray(bg_rho, dtype=np.float64)
@@ -138,7 +140,8 @@ def make_config(ndim, n, dx, *, variant="pvs", precision="fp64", xi=1.0, gamma=5
 def config_from_workload(w: dict, precision="fp64", **over):
     args = dict(variant=w["variant"], precision=precision, xi=w["xi"], gamma=w["gamma"], cfl=w.get("cfl", 0.4),
                 grav=w["grav"], bc=w["bc"], vertical=w["vertical"] if w["bg_rho"] is not None else -1,
-                bg_rho=w["bg_rho"], bg_p=w["bg_p"], cmax=w.get("cmax") or 0.0, cfl_rule=w.get("cfl_rule", 0))
+                bg_rho=w["bg_rho"], bg_p=w["bg_p"], cmax=w.get("cmax") or 0.0, cfl_rule=w.get("cfl_rule", 0),
+                covolume=w.get("covolume") or 0.0)
     args.update(over)
     return make_config(w["ndim"], w["n"], w["dx"], **args)
 

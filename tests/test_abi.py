@@ -38,7 +38,7 @@ def test_every_declared_symbol_is_exported(L):
 
 
 def test_config_layout(L):
-    assert L.rsst_config_size() == 144
+    assert L.rsst_config_size() == 152
 
 
 @pytest.mark.parametrize("bad", [dict(ndim=4), dict(xi=0.5), dict(gamma=1.0), dict(variant="bogus"),
@@ -59,6 +59,27 @@ def test_invalid_config_rejected_without_gpu(L, bad):
     with pytest.raises(rsst.RsstError) as e:
         rsst.rsst_init(cfg, stream=0)
     assert e.value.code == rsst.RSST_EINVAL
+
+
+@pytest.mark.parametrize("cov,precision,code", [(-0.1, "fp64", "RSST_EINVAL"), (float("nan"), "fp64", "RSST_EINVAL"),
+                                                (0.1, "fp32_pert", "RSST_EUNSUPPORTED"),
+                                                (0.1, "fp64_df", "RSST_EUNSUPPORTED")])
+def test_covolume_checked_without_gpu(L, cov, precision, code):
+    """The covolume gas: b >= 0 and finite, and only in the float64 precision."""
+    cfg = rsst.make_config(2, [8, 8, 1], [0.1, 0.1, 0.1], xi=3.0, precision=precision, covolume=cov)
+    with pytest.raises(rsst.RsstError) as e:
+        rsst.rsst_init(cfg, stream=0)
+    assert e.value.code == getattr(rsst, code)
+
+
+def test_background_beyond_the_covolume_rejected_without_gpu(L):
+    """A background density with b rho0 >= 1 is outside the covolume gas."""
+    rho, p = np.linspace(2.0, 1.0, 12), np.linspace(3.0, 1.0, 12)
+    cfg = rsst.make_config(2, [6, 8, 1], [0.1, 0.1, 0.1], xi=3.0, bc=("periodic", "reflect"), vertical=1,
+                           bg_rho=rho, bg_p=p, covolume=0.5)
+    with pytest.raises(rsst.RsstError) as e:
+        rsst.rsst_init(cfg, stream=0)
+    assert e.value.code == rsst.RSST_EINVAL and "covolume" in str(e.value)
 
 
 @pytest.mark.parametrize("bc,k,field,value", [("reflect", 0, "rho", -1.0), ("reflect", 11, "p", 0.0),

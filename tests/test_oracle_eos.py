@@ -1,8 +1,8 @@
 """General equation of state (Sec. 3.2: the reduced equations and the
 pressure tendency, Eqs. pvs_cons_dpr / pvs_cons_therm, are stated for any EOS).
-The paper specifies no non-ideal gas, so the product runs the ideal gas; here
-the oracle's EOS interface is exercised with a test-only covolume (Noble-Abel)
-gas, P = (gamma - 1) e / (1 - b rho), a^2 = gamma P / (rho (1 - b rho)),
+The paper specifies no non-ideal gas with parameters; the covolume
+(Noble-Abel) gas of oracle/eos.py (also selectable on the float64 device
+path through rsst_config.covolume) exercises the general formulas, P = (gamma - 1) e / (1 - b rho), a^2 = gamma P / (rho (1 - b rho)),
 (de/dP)_rho = (1 - b rho)/(gamma - 1), (de/drho)_P = -b P/(gamma - 1), to pin
 the general formulas: the pressure tendency equals the chain rule of P(U), the
 P-forms reduce dP/dt by xi^2, the entropy tendency is unchanged (except PD),
@@ -14,30 +14,11 @@ import pytest
 import torch
 
 from oracle import rsst_oracle as ro
+from oracle.eos import NobleAbel
 from oracle.workload import problem_from
 from paper_1812_04135_gb300 import inputs
 
 G = 1.4
-
-
-class NobleAbel:
-    def __init__(self, gamma, b):
-        self.gamma, self.b = gamma, b
-
-    def pressure(self, rho, eint):
-        return (self.gamma - 1.0) * eint / (1.0 - self.b * rho)
-
-    def internal_energy(self, rho, P):
-        return P * (1.0 - self.b * rho) / (self.gamma - 1.0)
-
-    def sound2(self, rho, P):
-        return self.gamma * P / (rho * (1.0 - self.b * rho))
-
-    def de_dP(self, rho, P):
-        return (1.0 - self.b * rho) / (self.gamma - 1.0)
-
-    def de_drho(self, rho, P):
-        return -self.b * P / (self.gamma - 1.0)
 
 
 EOS = NobleAbel(G, 0.15)
