@@ -549,8 +549,8 @@ extern "C" int rsst_debug_stall_wait(rsst_handle* h, int64_t limit_ns) {
     rsst_set_error("rsst_debug_stall_wait: need a handle and 0 <= limit_ns <= 1e9");
     return RSST_EINVAL;
   }
-  if (!h->use_tma2d) {
-    rsst_set_error("rsst_debug_stall_wait: only runs on the 2D float32-perturbation TMA kernel have the test wait");
+  if (!h->use_tma2d && !h->use_tma3d) {
+    rsst_set_error("rsst_debug_stall_wait: only runs on the float32-perturbation TMA kernels have the test wait");
     return RSST_EUNSUPPORTED;
   }
   if (limit_ns != h->stall_ns) drop_graphs(h);  // graphs hold the stage arguments by value

@@ -50,7 +50,7 @@ struct T3 {
   static constexpr int NCHUNK = (BY * CW - 1 + 30) / 31;
   static constexpr size_t RING = (size_t)NS * PLANE * 4;
   static constexpr size_t SCRATCH = RING + (size_t)(FX_FLOATS + FY_FLOATS + Q_FLOATS + TAB_FLOATS) * 4;
-  static constexpr size_t SMEM = SCRATCH + NS * 8 + 16 + 8 * 8 + 128;
+  static constexpr size_t SMEM = SCRATCH + NS * 8 + 16 + 8 * 8 + 8 + 128;  // ring barriers, dt, reduction, test barrier
   static constexpr uint32_t BOX_BYTES = PLANE * 4;
   static_assert(BX == 32, "one warp per row of the column block");
   static_assert(RING % 16 == 0 && (FX_FLOATS + FY_FLOATS + Q_FLOATS) % 4 == 0, "table rows on a 16-byte boundary");
@@ -137,6 +137,22 @@ __global__ void __launch_bounds__(T3::NT, 5) stage3d_tma_kernel(const __grid_con
   if (__syncthreads_or(!wait_upto(pfirst + 3))) {
     give_up();
     return;
+  }
+  if (a.stall_ns > 0) {
+    // Failure-detection test: wait on a barrier that expects 16 bytes no copy
+    // delivers; the wait runs out with the next plane's copy possibly still
+    // in flight, so the give-up path (flag, drain, return) runs in full.
+    uint64_t* sb = reinterpret_cast<uint64_t*>(smem_raw + T3::SCRATCH + T3::NS * 8 + 16 + 8 * 8);
+    if (tid == 0) {
+      mbar_init(sb, 1);
+      fence_mbar_init();
+      mbar_expect_tx(sb, 16);
+    }
+    __syncthreads();
+    if (__syncthreads_or(!mbar_wait_bounded(sb, 0u, (uint64_t)a.stall_ns))) {
+      give_up();
+      return;
+    }
   }
 
   const int cx = lane, cy = tid >> 5;

@@ -61,6 +61,29 @@ def test_single_run_wait_runs_out_and_is_reported(stage_steps):
     torch.cuda.synchronize()
 
 
+def test_3d_wait_runs_out_drains_and_is_reported():
+    """The 3D z-march: the test wait runs out after the first planes have
+    landed, with the next plane's copy issued; the kernel drains it, flags
+    the run and returns.  A fresh state then steps to the oracle's result."""
+    w = inputs.polytrope_3d(40, 12, 37, xi=50.0, amp=1e-3, contrast=20.0)
+    U = torch.from_numpy(w["U"]).cuda()
+    s = rsst.Solver(w, "fp32_pert")
+    try:
+        s.set_state(U)
+        rsst.rsst_debug_stall_wait(s.h, LIMIT_NS)
+        s.step(1)
+        with pytest.raises(rsst.RsstError) as e:
+            s.sync()
+        assert e.value.code == rsst.RSST_ETIMEOUT, str(e.value)
+        rsst.rsst_debug_stall_wait(s.h, 0)
+        s.set_state(U)
+        s.step(2)
+        err = rel_linf(s.get_state("cpu"), _oracle(w, 2), w["gamma"])
+        assert max(err) < 1e-5, err
+    finally:
+        s.close()
+
+
 def test_stall_hook_validation():
     w = inputs.shear_layer_2d(64, 32, xi=30.0, variant="pvs")
     s = rsst.Solver(w, "fp32_pert")
