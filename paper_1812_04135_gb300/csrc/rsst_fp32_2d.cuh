@@ -39,8 +39,11 @@ struct T2Cfg {
   static constexpr size_t SCRATCH = (size_t)(U_FLOATS + FX_FLOATS + TAB_FLOATS) * 4;
   // x-face pass: the slope cells -1 .. BX of every row, in one flat list
   // walked by warps in chunks of 32 cells that overlap by one
-  static constexpr int CW = BX + 2;
-  static constexpr int NCHUNK = (BY * CW - 1 + 30) / 31;
+  // x-face pass: the slope cells -1 .. BX of every row (padded to CW2, an
+  // even count, with two cells beyond BX) form one flat list; a lane takes
+  // two neighbouring cells, a warp chunk 64 cells, chunks start every 62
+  static constexpr int CW2 = BX + 4;
+  static constexpr int NCHUNK2 = (BY * CW2 - 2 + 61) / 62;
   static constexpr uint32_t BOX_BYTES = U_FLOATS * 4;
   static constexpr size_t smem_bytes() { return SCRATCH + 16 + 8 * 8 + 512 + 128; }
   static_assert(BY % SEG == 0, "column segments must tile BY");
@@ -149,39 +152,51 @@ __device__ __forceinline__ bool tile2d_f(const CUtensorMap* tin, const TileRun& 
 
   const int nx = g.n[0], ny = g.n[1];
   const int lane = tid & 31;
-  // ---- x faces.  The slope cells -1 .. BX of every row form one flat list;
-  // chunk k holds cells 31k .. 31k + 31 (lane l: cell 31k + l).  Each lane
-  // takes its cell's half slope: its right state U - h is the right state of
-  // the face on the cell's left, and U + h, passed one lane up, the left
-  // state of that face for the next lane.  Lanes 1..31 thus get every face
-  // of the row (faces 0 .. BX), no lane recomputes a slope, and no lane runs
-  // alone; a lane whose two cells lie in different rows has no face.
+  // ---- x faces.  The slope cells of every row form one flat list; chunk k
+  // holds cells 62k .. 62k + 63, lane l the pair A = 62k + 2l, A + 1 (a pair
+  // never straddles two rows: the rows hold an even number of cells).  The
+  // lane takes both cells' half slopes (four loads and three differences per
+  // field), forms the face between its two cells, and the face on A's left
+  // from its own state A - h_A and the state B + h_B passed one lane up.  So
+  // every face of the tile is formed (the two cells shared by consecutive
+  // chunks give one face twice, with equal values), no slope is recomputed
+  // within a chunk and no lane runs alone; lane 0's left face and faces
+  // across rows are left out.
   {
     const int nwarp = T2::NT / 32;
-    for (int k = tid >> 5; k < T2::NCHUNK; k += nwarp) {
-      int F = 31 * k + lane;
-      const bool inb = F < T2::BY * T2::CW;
-      F = inb ? F : T2::BY * T2::CW - 1;  // keeps the loads inside the box
-      const int row = F / T2::CW;
-      const int cc = F - row * T2::CW - 1;  // tile column -1 .. BX
+    for (int k = tid >> 5; k < T2::NCHUNK2; k += nwarp) {
+      int A = 62 * k + 2 * lane;  // my two cells A, A + 1 (same row: rows hold an even CW2 cells)
+      const bool inb = A < T2::BY * T2::CW2;
+      A = inb ? A : T2::BY * T2::CW2 - 2;  // keeps the loads inside the box
+      const int row = A / T2::CW2;
+      const int ca = A - row * T2::CW2 - 1;  // tile column of A: -1 .. BX + 1
       const int sr = row + 2;
-      const float* ur = sU + sr * T2::SXP + T2::XO + cc;
-      float qR[NV], qL[NV];
+      const float* ur = sU + sr * T2::SXP + T2::XO + ca;
+      float qRl[NV], qLl[NV], qLi[NV], qRi[NV];
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
         const float* uv = ur + v * PL;
-        const float um = uv[-1], u0 = uv[0], up = uv[1];
-        const float h = half_mc_f(u0 - um, up - u0);
-        qR[v] = u0 - h;
-        qL[v] = __shfl_up_sync(0xffffffffu, u0 + h, 1);
+        const float am = uv[-1], a = uv[0], b = uv[1], bp = uv[2];
+        const float d1 = a - am, d2 = b - a, d3 = bp - b;
+        const float ha = half_mc_f(d1, d2), hb = half_mc_f(d2, d3);
+        qRl[v] = a - ha;
+        qLi[v] = a + ha;
+        qRi[v] = b - hb;
+        qLl[v] = __shfl_up_sync(0xffffffffu, b + hb, 1);
       }
       float4 cb = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
       if constexpr (BG) cb = *reinterpret_cast<const float4*>(st + sr * TR_W + TR_RHO0);
+      const bool rowok = inb && j0 + row < ny;
       float G[NV];
-      face_flat_cm<NV, 0, BG, CM>(qL, qR, cb, pf, G);
-      if (inb && lane > 0 && cc >= 0 && i0 + cc <= nx && j0 + row < ny) {
+      face_flat_cm<NV, 0, BG, CM>(qLi, qRi, cb, pf, G);  // face between A and A + 1: face index ca + 1
+      if (rowok && ca + 1 <= T2::BX && i0 + ca + 1 <= nx) {
 #pragma unroll
-        for (int v = 0; v < NV; ++v) sFx[(v * T2::BY + row) * T2::FXW + cc] = G[v];
+        for (int v = 0; v < NV; ++v) sFx[(v * T2::BY + row) * T2::FXW + ca + 1] = G[v];
+      }
+      face_flat_cm<NV, 0, BG, CM>(qLl, qRl, cb, pf, G);  // face between A - 1 and A: face index ca
+      if (rowok && lane > 0 && ca >= 0 && ca <= T2::BX && i0 + ca <= nx) {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) sFx[(v * T2::BY + row) * T2::FXW + ca] = G[v];
       }
     }
   }

@@ -13,10 +13,10 @@
 //      the plane also publishes these states);
 //   B. every thread forms twice the LLF flux of the y face below its cell
 //      from the state written by the cell below (the last warp also the
-//      face above the block), and the warps walk the x faces of the plane in chunks of 32
-//      slope cells overlapping by one (as in the 2D kernel: each lane's half
-//      slope gives its face's right state and, one lane up, the next face's
-//      left state, so 31 lanes of 32 form a face and no lane runs alone);
+//      face above the block), and the warps walk the x faces of the plane in
+//      chunks of 64 slope cells, two per lane (as in the 2D kernel: a lane
+//      forms the face between its cells and, with the state passed one lane
+//      up, the face on its left; no lane runs alone);
 //   C. each thread advances its column: one new z half slope and z-face flux
 //      from a register window, the divergence (its x and y faces from shared
 //      memory), the reduced tendency, force, RK combine, store and edge
@@ -46,8 +46,8 @@ struct T3 {
   static constexpr int Q_FLOATS = NV * QROWS * BX;
   static constexpr int TROWS = CZ + 4;
   static constexpr int TAB_FLOATS = TR_W * TROWS;
-  static constexpr int CW = BX + 2;        // x slope cells per row (-1 .. BX)
-  static constexpr int NCHUNK = (BY * CW - 1 + 30) / 31;
+  static constexpr int CW2 = BX + 4;       // x slope cells per row (-1 .. BX, padded to an even count)
+  static constexpr int NCHUNK2 = (BY * CW2 - 2 + 61) / 62;  // chunks of 64 cells, one every 62
   static constexpr size_t RING = (size_t)NS * PLANE * 4;
   static constexpr size_t SCRATCH = RING + (size_t)(FX_FLOATS + FY_FLOATS + Q_FLOATS + TAB_FLOATS) * 4;
   static constexpr size_t SMEM = SCRATCH + NS * 8 + 16 + 8 * 8 + 8 + 128;  // ring barriers, dt, reduction, test barrier
@@ -259,26 +259,34 @@ __global__ void __launch_bounds__(T3::NT, 5) stage3d_tma_kernel(const __grid_con
 #pragma unroll
         for (int v = 0; v < NV; ++v) sFy[(v * (T3::BY + 1) + T3::BY) * T3::BX + cx] = G[v];
       }
-      for (int c = cy; c < T3::NCHUNK; c += T3::NT / 32) {
-        int F = 31 * c + lane;
-        const bool inb = F < T3::BY * T3::CW;
-        F = inb ? F : T3::BY * T3::CW - 1;  // keeps the loads inside the box
-        const int row = F / T3::CW;
-        const int cc = F - row * T3::CW - 1;  // tile column -1 .. BX
-        const float* ur = P + (row + T3::YO) * T3::SXP + T3::XO + cc;
-        float qR[NV], qL[NV], G[NV];
+      for (int c = cy; c < T3::NCHUNK2; c += T3::NT / 32) {
+        int A = 62 * c + 2 * lane;  // my two cells A, A + 1 (same row)
+        const bool inb = A < T3::BY * T3::CW2;
+        A = inb ? A : T3::BY * T3::CW2 - 2;  // keeps the loads inside the box
+        const int row = A / T3::CW2;
+        const int ca = A - row * T3::CW2 - 1;  // tile column of A: -1 .. BX + 1
+        const float* ur = P + (row + T3::YO) * T3::SXP + T3::XO + ca;
+        float qRl[NV], qLl[NV], qLi[NV], qRi[NV], G[NV];
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
           const float* uv = ur + v * T3::PF;
-          const float um = uv[-1], u = uv[0], up = uv[1];
-          const float h = half_mc_f(u - um, up - u);
-          qR[v] = u - h;
-          qL[v] = __shfl_up_sync(0xffffffffu, u + h, 1);
+          const float am = uv[-1], ua = uv[0], ub = uv[1], bp = uv[2];
+          const float d1 = ua - am, d2 = ub - ua, d3 = bp - ub;
+          const float ha = half_mc_f(d1, d2), hb = half_mc_f(d2, d3);
+          qRl[v] = ua - ha;
+          qLi[v] = ua + ha;
+          qRi[v] = ub - hb;
+          qLl[v] = __shfl_up_sync(0xffffffffu, ub + hb, 1);
         }
-        face_flat_cm<NV, 0, BG, CM>(qL, qR, cb, pf, G);
-        if (inb && lane > 0 && cc >= 0) {
+        face_flat_cm<NV, 0, BG, CM>(qLi, qRi, cb, pf, G);  // face between A and A + 1: index ca + 1
+        if (inb && ca + 1 <= T3::BX) {
 #pragma unroll
-          for (int v = 0; v < NV; ++v) sFx[(v * T3::BY + row) * T3::FXW + cc] = G[v];
+          for (int v = 0; v < NV; ++v) sFx[(v * T3::BY + row) * T3::FXW + ca + 1] = G[v];
+        }
+        face_flat_cm<NV, 0, BG, CM>(qLl, qRl, cb, pf, G);  // face between A - 1 and A: index ca
+        if (inb && lane > 0 && ca >= 0 && ca <= T3::BX) {
+#pragma unroll
+          for (int v = 0; v < NV; ++v) sFx[(v * T3::BY + row) * T3::FXW + ca] = G[v];
         }
       }
     }
