@@ -1,7 +1,8 @@
 // Float32 perturbation stage kernel for 3D grids: TMA-streamed z-march.
 //
 // A CTA owns a BX x BY = 32 x 4 block of (x, y) columns (one warp per row of
-// the block) and a chunk of CZ = 16 z-planes.  Planes (two-cell x/y halos,
+// the block) and a chunk of CZ = 12 z-planes (the best of 8, 11, 12 and 16
+// planes, and of 32 x 8 blocks, on the 256 x 128 x 128 workload).  Planes (two-cell x/y halos,
 // all five fields; x origin rounded down to a 16-byte boundary) stream
 // through an NS = 5 slot shared-memory ring, one cp.async.bulk.tensor per
 // plane issued three planes ahead, each slot with its own mbarrier (bounded
@@ -35,7 +36,7 @@
 namespace rsst {
 
 struct T3 {
-  static constexpr int NV = 5, BX = 32, BY = 4, NT = BX * BY, CZ = 16, NS = 5;
+  static constexpr int NV = 5, BX = 32, BY = 4, NT = BX * BY, CZ = 12, NS = 5;
   static constexpr int SXP = BX + 8, SYP = BY + 4, XO = 4, YO = 2;
   static constexpr int PF = SYP * SXP;     // floats per field in a plane slot
   static constexpr int PLANE = NV * PF;    // floats per plane slot
