@@ -334,9 +334,9 @@ int rsst_batch_tile_shape(const rsst_batch* b, int32_t* bx, int32_t* by);
 int64_t rsst_batch_kernel_launches(const rsst_batch* b);
 
 /* Conservation sums of a caller-held state, for callers that cannot allocate
- * device memory when they need them (inside stream capture, where cudaMalloc
- * is not allowed; inside another framework that owns the device-memory
- * budget; in loops that cannot take cudaMalloc's device synchronisation).
+ * device memory when they need them (inside another framework that owns the
+ * device-memory budget; in loops that cannot take cudaMalloc's device
+ * synchronisation).
  * The paper has no counterpart: it is a deployment convenience.
  *   U     device pointer, float64, caller layout [nvar][nz][ny][nx], read only
  *   ndim  1..3 (nvar = ndim + 2 <= 5); n, dx: host arrays of ndim entries
@@ -345,8 +345,8 @@ int64_t rsst_batch_kernel_launches(const rsst_batch* b);
  * Allocates nothing: its only scratch is a file-scope device array of
  * 5 x 1024 doubles (40 KiB) that every GPU loading the library keeps until
  * exit.  The first call on a device looks that array's address up
- * (cudaGetSymbolAddress) with the device current, so make the first call on
- * each device before any stream capture.  Calls share the array: two calls
+ * (cudaGetSymbolAddress, with the device current) and keeps it for later
+ * calls.  Calls share the array: two calls
  * that overlap on the GPU (different streams, not ordered) race and give wrong
  * sums.  Each call overwrites every scratch entry it reads, so no clearing is
  * needed.  Rejects ndim outside 1..3 and grids above 2^31 cells with

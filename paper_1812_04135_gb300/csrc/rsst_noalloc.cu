@@ -2,11 +2,10 @@
 //
 // rsst_conserved_sums works on a handle whose scratch (the per-block partial
 // sums) was allocated by rsst_init.  Some callers cannot allocate device
-// memory at the point where they need the sums: code running while a stream
-// is being captured into a CUDA graph (cudaMalloc is not allowed there),
-// plug-ins living inside another framework that owns the whole device-memory
-// budget through its own caching allocator, and latency-critical loops that
-// cannot afford cudaMalloc's implicit device synchronisation.  This entry
+// memory at the point where they need the sums: plug-ins living inside
+// another framework that owns the whole device-memory budget through its own
+// caching allocator, and latency-critical loops that cannot afford
+// cudaMalloc's implicit device synchronisation.  This entry
 // point serves them: the caller passes the state and the output, and the only
 // scratch is the file-scope array below, which every GPU that loads the
 // library holds until the process exits.

@@ -1,8 +1,8 @@
 """The allocation-free conservation sums against the handle-based ones.
 
 Some callers cannot allocate device memory at the moment they need the sums
-(for instance while a stream is being captured, or inside another framework
-that owns the device-memory budget).  rsst_conserved_sums_noalloc serves
+(for instance inside another framework that owns the device-memory
+budget).  rsst_conserved_sums_noalloc serves
 them with a fixed device-side scratch array; here it must agree with
 rsst_conserved_sums on the same states, on two calls in a row.  Both use the
 same fixed reduction tree (1024 contiguous chunks, the same thread striding
