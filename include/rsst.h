@@ -189,19 +189,20 @@ int rsst_time(rsst_handle* h, double* t);
 int rsst_sync(rsst_handle* h);
 
 /* Failure-detection test hook (no counterpart in the paper).  With
- * limit_ns > 0, from the next step on every tile of the RSST_FP32_PERT TMA
- * stage kernels also waits up to limit_ns on a shared-memory barrier that
- * nothing completes: in 2D once its own copy has landed (so no copy is in
- * flight), in 3D after its first planes have landed (the next plane's copy
- * may still be in flight, and the kernel waits for it before leaving).  The
- * wait runs out, the kernel sets the run's timeout flag and returns without
- * writing that tile, and the next synchronous call returns RSST_ETIMEOUT;
- * the state is then incomplete (load one with rsst_set_state).
- * limit_ns = 0 restores normal steps.  Errors: RSST_EINVAL unless
- * 0 <= limit_ns <= 1e9; RSST_EUNSUPPORTED for runs that do not use those
- * kernels (they serve 2D RSST_FP32_PERT runs with vertical axis y or none
- * and 3D ones with vertical axis z or none).  Synchronous, launches
- * nothing. */
+ * limit_ns > 0, from the next step on every tile of the TMA-staged stage
+ * kernels also waits up to limit_ns on a shared-memory barrier that nothing
+ * completes: in the 2D RSST_FP32_PERT kernel once its own copy has landed
+ * (so no copy is in flight), in the 3D one after its first planes have
+ * landed (the next plane's copy may still be in flight), and in the 2D/3D
+ * RSST_FP64 kernel while its tile copy is in flight; a kernel waits for
+ * copies it issued before leaving.  The wait runs out, the kernel sets the
+ * run's timeout flag and returns without writing that tile, and the next
+ * synchronous call returns RSST_ETIMEOUT; the state is then incomplete (load
+ * one with rsst_set_state).  limit_ns = 0 restores normal steps.  Errors:
+ * RSST_EINVAL unless 0 <= limit_ns <= 1e9; RSST_EUNSUPPORTED for runs that
+ * do not use those kernels (they serve 2D RSST_FP32_PERT runs with vertical
+ * axis y or none, 3D ones with vertical axis z or none, and 2D/3D RSST_FP64
+ * runs).  Synchronous, launches nothing. */
 int rsst_debug_stall_wait(rsst_handle* h, int64_t limit_ns);
 
 /* Sum over cells of each conserved variable times the cell volume, in

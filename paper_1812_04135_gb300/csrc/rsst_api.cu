@@ -115,6 +115,28 @@ static int make_tmap_2d(CUtensorMap* m, void* base, const Geom& g, int nv, int b
   return RSST_OK;
 }
 
+// Tiled float64 map of a padded 2D/3D state [nvar][pz][py][pitch]: the
+// float64 stage kernel's halo tile (box sx x sy [x sz]) of every field.
+static int make_tmap_f64(CUtensorMap* m, void* base, const Geom& g, int nv) {
+  auto enc = tensor_map_encoder();
+  if (!enc) { rsst_set_error("cuTensorMapEncodeTiled unavailable from the CUDA driver"); return RSST_ECUDA; }
+  int sx, sy, sz;
+  rsst_stage_fp64_box(g.ndim, &sx, &sy, &sz);
+  const bool d3 = g.ndim == 3;
+  const cuuint32_t rank = d3 ? 4 : 3;
+  const cuuint64_t dims[4] = {(cuuint64_t)g.pitch, (cuuint64_t)g.py, d3 ? (cuuint64_t)g.pz : (cuuint64_t)nv,
+                              (cuuint64_t)nv};
+  const cuuint64_t strides[3] = {(cuuint64_t)g.pitch * 8, d3 ? (cuuint64_t)g.plane * 8 : (cuuint64_t)g.fstride * 8,
+                                 (cuuint64_t)g.fstride * 8};
+  const cuuint32_t box[4] = {(cuuint32_t)sx, (cuuint32_t)sy, d3 ? (cuuint32_t)sz : (cuuint32_t)nv, (cuuint32_t)nv};
+  const cuuint32_t estr[4] = {1, 1, 1, 1};
+  const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, rank, base, dims, strides, box, estr,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) { rsst_set_error("cuTensorMapEncodeTiled (float64) failed (%d)", (int)r); return RSST_ECUDA; }
+  return RSST_OK;
+}
+
 static int validate(const rsst_config* c) {
   if (!c) { rsst_set_error("config is NULL"); return RSST_EINVAL; }
   if (c->covolume != 0.0 && c->precision != RSST_FP64) {
@@ -331,6 +353,13 @@ extern "C" int rsst_init(rsst_handle** out, const rsst_config* cfg, void* stream
       if (rc != RSST_OK) goto fail;
     }
   }
+  if (cfg->precision == RSST_FP64 && cfg->ndim >= 2) {
+    h->use_tma_fp64 = 1;
+    for (int b = 0; b < 2; ++b) {
+      rc = make_tmap_f64(&h->tmap[b], h->buf[b], h->g, nv);
+      if (rc != RSST_OK) goto fail;
+    }
+  }
   if (cfg->precision == RSST_FP32_PERT && cfg->ndim == 3 && (cfg->vertical == -1 || cfg->vertical == 2)) {
     h->use_tma3d = 1;
     for (int b = 0; b < 2; ++b) {
@@ -444,7 +473,7 @@ static int plain_steps(rsst_handle* h, double dt, int nsteps, cudaStream_t st) {
     a.base = nullptr;
     a.out = Us;
     a.dU_out = h->rec_dU[0];
-    if constexpr (std::is_same<T, double>::value) RC_TRY(rsst_launch_stage_fp64(a, st));
+    if constexpr (std::is_same<T, double>::value) RC_TRY(rsst_launch_stage_fp64(h->use_tma_fp64 ? &h->tmap[0] : nullptr, a, st));
     else if constexpr (std::is_same<T, float2>::value) RC_TRY(rsst_launch_stage_df(a, st));
     else if (h->use_tma2d) RC_TRY(rsst_launch_stage2d_tma(&h->tmap[0], a, st));
     else if (h->use_tma3d) RC_TRY(rsst_launch_stage3d_tma(&h->tmap[0], a, st));
@@ -454,7 +483,7 @@ static int plain_steps(rsst_handle* h, double dt, int nsteps, cudaStream_t st) {
     a.base = U;
     a.out = U;
     a.dU_out = h->rec_dU[1];
-    if constexpr (std::is_same<T, double>::value) RC_TRY(rsst_launch_stage_fp64(a, st));
+    if constexpr (std::is_same<T, double>::value) RC_TRY(rsst_launch_stage_fp64(h->use_tma_fp64 ? &h->tmap[1] : nullptr, a, st));
     else if constexpr (std::is_same<T, float2>::value) RC_TRY(rsst_launch_stage_df(a, st));
     else if (h->use_tma2d) RC_TRY(rsst_launch_stage2d_tma(&h->tmap[1], a, st));
     else if (h->use_tma3d) RC_TRY(rsst_launch_stage3d_tma(&h->tmap[1], a, st));
@@ -549,8 +578,8 @@ extern "C" int rsst_debug_stall_wait(rsst_handle* h, int64_t limit_ns) {
     rsst_set_error("rsst_debug_stall_wait: need a handle and 0 <= limit_ns <= 1e9");
     return RSST_EINVAL;
   }
-  if (!h->use_tma2d && !h->use_tma3d) {
-    rsst_set_error("rsst_debug_stall_wait: only runs on the float32-perturbation TMA kernels have the test wait");
+  if (!h->use_tma2d && !h->use_tma3d && !h->use_tma_fp64) {
+    rsst_set_error("rsst_debug_stall_wait: only runs on the TMA-staged kernels (float32 perturbation 2D/3D, float64 2D/3D) have the test wait");
     return RSST_EUNSUPPORTED;
   }
   if (limit_ns != h->stall_ns) drop_graphs(h);  // graphs hold the stage arguments by value

@@ -4,7 +4,11 @@
 //
 // Fused stage kernel, one CTA per tile of BX x BY x BZ cells:
 //   1. the tile plus two halo layers on every active axis (all fields) is
-//      copied from the padded state into shared memory with coalesced loads;
+//      copied from the padded state into shared memory: in 2D and 3D by one
+//      cp.async.bulk.tensor of the whole box (x origin on a 16-byte
+//      boundary, rows and planes beyond the padded state zero-filled, a
+//      bounded mbarrier wait), in 1D (tiles wider than a TMA box) with
+//      coalesced loads;
 //   2. per axis D, the MC slope of every cell along D is computed once into
 //      shared memory (1D/2D tiles and small 3D tiles; larger 3D tiles take
 //      the two slopes per face), then every face of the tile gets twice its
@@ -22,6 +26,7 @@
 #include "rsst_internal.h"
 #include "rsst_attr.h"
 #include "rsst_math_fp64.cuh"
+#include "rsst_tma.cuh"
 
 namespace rsst {
 
@@ -90,11 +95,17 @@ struct TileCfg {
   static constexpr bool SLOPES =
       NDIM <= 2 || sizeof(double) * (size_t)NV * (SCELLS + FMAX + EXM) <= (size_t)76 * 1024;
   static constexpr int SEMAX = SLOPES ? EXM : 0;
-  static constexpr size_t SMEM = sizeof(double) * (size_t)NV * (SCELLS + FMAX + SEMAX) + 64 * sizeof(double);
+  // halo tile, faces, slopes, the block reduction's 64 doubles, and two
+  // mbarriers (the tile copy; the failure-detection test wait)
+  static constexpr size_t SMEM = sizeof(double) * (size_t)NV * (SCELLS + FMAX + SEMAX) + 64 * sizeof(double) + 16;
+  static constexpr uint32_t TILE_BYTES = (uint32_t)(sizeof(double) * NV * SCELLS);
+  static_assert(NDIM == 1 || (SX <= 256 && SY <= 256 && SZ <= 256), "TMA box dimensions are at most 256");
+  static_assert((SX * sizeof(double)) % 16 == 0 && (HX * sizeof(double)) % 16 == 0,
+                "the box's row bytes and the x origin (interior x0 - HX) stay on 16-byte boundaries");
 };
 
 // Faces along axis D of the tile: index space (BX + [D==0]) x (BY + [D==1]) x (BZ + [D==2]).
-template <int NDIM, int BX, int BY, int BZ, int NT, int D>
+template <int NDIM, int BX, int BY, int BZ, int NT, int D, bool CV>
 __device__ __forceinline__ void face_pass(const double* __restrict__ su, double* __restrict__ sf,
                                           double* __restrict__ ss, const Phys& p, const Geom& g, int i0, int j0,
                                           int k0, double (&dU)[TileCfg<NDIM, BX, BY, BZ, NT>::CPT][NDIM + 2]) {
@@ -159,7 +170,7 @@ __device__ __forceinline__ void face_pass(const double* __restrict__ su, double*
       }
     }
     double F[NV];  // twice the face flux
-    llf_flux_x2<NV, D>(qL, qR, p, F);
+    llf_flux_x2<NV, D, CV>(qL, qR, p, F);
 #pragma unroll
     for (int v = 0; v < NV; ++v) sf[v * C::FMAX + fid] = F[v];
   }
@@ -181,11 +192,12 @@ __device__ __forceinline__ void face_pass(const double* __restrict__ su, double*
   __syncthreads();
 }
 
-template <int NDIM, int BX, int BY, int BZ, int NT>
-__global__ void __launch_bounds__(NT, NDIM == 3 ? 3 : 0) stage_fp64_kernel(const StageArgs<double> a) {
+template <int NDIM, int BX, int BY, int BZ, int NT, bool TMA, bool CV>
+__global__ void __launch_bounds__(NT, NDIM == 3 ? 3 : 0)
+    stage_fp64_kernel(const __grid_constant__ CUtensorMap tin, const StageArgs<double> a) {
   using C = TileCfg<NDIM, BX, BY, BZ, NT>;
   constexpr int NV = C::NV;
-  extern __shared__ double smem[];
+  extern __shared__ __align__(128) double smem[];
   double* su = smem;
   double* sf = smem + NV * C::SCELLS;
   double* ss = sf + NV * C::FMAX;  // slopes (1D/2D tiles)
@@ -195,6 +207,40 @@ __global__ void __launch_bounds__(NT, NDIM == 3 ? 3 : 0) stage_fp64_kernel(const
   const int i0 = blockIdx.x * BX, j0 = blockIdx.y * BY, k0 = blockIdx.z * BZ;
 
   // 1. halo tile -> shared memory
+  if constexpr (TMA) {
+    // The box of the padded state [nvar][pz][py][pitch] whose first cell is
+    // interior (i0 - HX, j0 - HY, k0 - HZ): padded x i0 + xoff - HX, padded
+    // y j0 (HY = gy), padded z k0 (HZ = gz).
+    uint64_t* bar = reinterpret_cast<uint64_t*>(sred + 64);
+    uint64_t* test_bar = bar + 1;
+    const bool stall = a.stall_ns > 0;
+    if (threadIdx.x == 0) {
+      mbar_init(bar, 1);
+      if (stall) mbar_init(test_bar, 1);
+      fence_mbar_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      fence_proxy_async_smem();
+      mbar_expect_tx(bar, C::TILE_BYTES);
+      if constexpr (NDIM == 2) tma_load_3d(su, &tin, bar, i0 + g.xoff - C::HX, j0, 0);
+      else tma_load_4d(su, &tin, bar, i0 + g.xoff - C::HX, j0, k0, 0);
+      // failure-detection test: a barrier that expects 16 bytes no copy
+      // delivers, waited on while the tile copy is still in flight
+      if (stall) mbar_expect_tx(test_bar, 16);
+    }
+    const bool landed = stall ? mbar_wait_bounded(test_bar, 0u, (uint64_t)a.stall_ns) : mbar_wait_bounded(bar, 0u);
+    // Giving up is decided by the whole block: flag the run and, before
+    // leaving, wait (bounded) for the tile copy, so that it cannot land in
+    // shared memory the next CTA on this SM may own.
+    if (__syncthreads_or(!landed)) {
+      if (threadIdx.x == 0) {
+        atomicOr(a.flag, RSST_FLAG_TIMEOUT);
+        mbar_wait_bounded(bar, 0u);
+      }
+      return;
+    }
+  } else {
   for (int id = threadIdx.x; id < NV * C::SCELLS; id += NT) {
     const int v = id / C::SCELLS;
     const int r = id - v * C::SCELLS;
@@ -209,6 +255,7 @@ __global__ void __launch_bounds__(NT, NDIM == 3 ? 3 : 0) stage_fp64_kernel(const
     su[id] = val;
   }
   __syncthreads();
+  }
 
   // 2-3. face fluxes and divergence, axis by axis
   double dU[C::CPT][NV];
@@ -216,9 +263,9 @@ __global__ void __launch_bounds__(NT, NDIM == 3 ? 3 : 0) stage_fp64_kernel(const
   for (int c = 0; c < C::CPT; ++c)
 #pragma unroll
     for (int v = 0; v < NV; ++v) dU[c][v] = 0.0;
-  face_pass<NDIM, BX, BY, BZ, NT, 0>(su, sf, ss, p, g, i0, j0, k0, dU);
-  if constexpr (NDIM >= 2) face_pass<NDIM, BX, BY, BZ, NT, 1>(su, sf, ss, p, g, i0, j0, k0, dU);
-  if constexpr (NDIM >= 3) face_pass<NDIM, BX, BY, BZ, NT, 2>(su, sf, ss, p, g, i0, j0, k0, dU);
+  face_pass<NDIM, BX, BY, BZ, NT, 0, CV>(su, sf, ss, p, g, i0, j0, k0, dU);
+  if constexpr (NDIM >= 2) face_pass<NDIM, BX, BY, BZ, NT, 1, CV>(su, sf, ss, p, g, i0, j0, k0, dU);
+  if constexpr (NDIM >= 3) face_pass<NDIM, BX, BY, BZ, NT, 2, CV>(su, sf, ss, p, g, i0, j0, k0, dU);
 
   // 4. epilogue
   const double dt = a.dt_fixed > 0.0 ? a.dt_fixed : p.cfl / a.scal[a.slot];
@@ -251,7 +298,7 @@ __global__ void __launch_bounds__(NT, NDIM == 3 ? 3 : 0) stage_fp64_kernel(const
 #pragma unroll
       for (int v = 0; v < NV; ++v) a.dU_out[v * g.fstride + o] = L[v];
     }
-    rsst_rhs<NV>(q, L, p);
+    rsst_rhs<NV, CV>(q, L, p);
     if (a.stage == 1) {
 #pragma unroll
       for (int v = 0; v < NV; ++v) u[v] = q[v] + dt * L[v];
@@ -260,7 +307,7 @@ __global__ void __launch_bounds__(NT, NDIM == 3 ? 3 : 0) stage_fp64_kernel(const
 #pragma unroll
       for (int v = 0; v < NV; ++v) u[v] = 0.5 * a.base[v * g.fstride + o] + 0.5 * (q[v] + dt * L[v]);
       bool ok;
-      const double r = cfl_rate<NV>(u, p, ok);
+      const double r = cfl_rate<NV, CV>(u, p, ok);
       if (ok) rmax = fmax(rmax, r);
       ok_all = ok_all && ok;
     }
@@ -331,7 +378,7 @@ __global__ void unpack_fp64_kernel(const double* __restrict__ src, double* __res
   }
 }
 
-template <int NV>
+template <int NV, bool CV>
 __global__ void __launch_bounds__(256) cfl_fp64_kernel(const double* __restrict__ U, Geom g, Phys p, double* dst,
                                                        unsigned int* flag) {
   __shared__ double sred[8];
@@ -346,7 +393,7 @@ __global__ void __launch_bounds__(256) cfl_fp64_kernel(const double* __restrict_
 #pragma unroll
     for (int v = 0; v < NV; ++v) q[v] = U[v * g.fstride + o];
     bool ok;
-    const double r = cfl_rate<NV>(q, p, ok);
+    const double r = cfl_rate<NV, CV>(q, p, ok);
     if (ok) rmax = fmax(rmax, r);
     ok_all = ok_all && ok;
   }
@@ -407,17 +454,18 @@ __global__ void __launch_bounds__(SUM_THREADS) sums_final_kernel(const double* _
 // Launchers
 // ---------------------------------------------------------------------------
 
-template <int NDIM, int BX, int BY, int BZ, int NT>
-static int launch_stage(const StageArgs<double>& a, cudaStream_t s) {
+template <int NDIM, int BX, int BY, int BZ, int NT, bool TMA, bool CV>
+static int launch_stage_eos(const CUtensorMap* tin, const StageArgs<double>& a, cudaStream_t s) {
   using C = TileCfg<NDIM, BX, BY, BZ, NT>;
-  auto kern = stage_fp64_kernel<NDIM, BX, BY, BZ, NT>;
+  auto kern = stage_fp64_kernel<NDIM, BX, BY, BZ, NT, TMA, CV>;
   static std::atomic<unsigned long long> attr{0};
   if (set_smem_limit_once(kern, C::SMEM, attr) != cudaSuccess) {
     rsst_set_error("cudaFuncSetAttribute failed for the float64 stage kernel");
     return RSST_ECUDA;
   }
+  static const CUtensorMap none = {};
   dim3 grid((a.g.n[0] + BX - 1) / BX, NDIM >= 2 ? (a.g.n[1] + BY - 1) / BY : 1, NDIM >= 3 ? (a.g.n[2] + BZ - 1) / BZ : 1);
-  kern<<<grid, NT, C::SMEM, s>>>(a);
+  kern<<<grid, NT, C::SMEM, s>>>(TMA ? *tin : none, a);
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
     rsst_set_error("float64 stage kernel launch: %s", cudaGetErrorString(e));
@@ -426,17 +474,39 @@ static int launch_stage(const StageArgs<double>& a, cudaStream_t s) {
   return RSST_OK;
 }
 
+// The gas law is a compile-time choice (no covolume arithmetic in ideal-gas runs).
+template <int NDIM, int BX, int BY, int BZ, int NT, bool TMA>
+static int launch_stage(const CUtensorMap* tin, const StageArgs<double>& a, cudaStream_t s) {
+  if (a.p.covol != 0.0) return launch_stage_eos<NDIM, BX, BY, BZ, NT, TMA, true>(tin, a, s);
+  return launch_stage_eos<NDIM, BX, BY, BZ, NT, TMA, false>(tin, a, s);
+}
+
 }  // namespace rsst
 
 using namespace rsst;
 
-int rsst_launch_stage_fp64(const StageArgs<double>& a, cudaStream_t s) {
+// Tiles: 1D short lines take 16-cell tiles (17 faces, one per thread of a
+// warp) to spread the float64 work over SMs, longer ones 256 cells; 2D 32 x 8
+// with 9 warps (every face and slope pass in one round); 3D 8 x 8 x 4 with
+// slopes in shared memory and 10 warps (each face pass in one round).
+using Tile2 = TileCfg<2, 32, 8, 1, 288>;
+using Tile3 = TileCfg<3, 8, 8, 4, 320>;
+
+void rsst_stage_fp64_box(int ndim, int* sx, int* sy, int* sz) {
+  *sx = ndim == 3 ? Tile3::SX : Tile2::SX;
+  *sy = ndim == 3 ? Tile3::SY : Tile2::SY;
+  *sz = ndim == 3 ? Tile3::SZ : 1;
+}
+
+int rsst_launch_stage_fp64(const CUtensorMap* tin, const StageArgs<double>& a, cudaStream_t s) {
   switch (a.g.ndim) {
-    case 1:  // short lines: 16-cell tiles (17 faces, one per thread of a warp) spread the float64 work over SMs
-      if (a.g.n[0] <= RSST_SMALL_1D) return launch_stage<1, 16, 1, 1, 32>(a, s);
-      return launch_stage<1, 256, 1, 1, 256>(a, s);
-    case 2: return launch_stage<2, 32, 8, 1, 288>(a, s);  // 9 warps: every face and slope pass in one round
-    case 3: return launch_stage<3, 8, 8, 4, 320>(a, s);  // slopes in shared memory; 10 warps: each face pass in one round
+    case 1:
+      if (a.g.n[0] <= RSST_SMALL_1D) return launch_stage<1, 16, 1, 1, 32, false>(nullptr, a, s);
+      return launch_stage<1, 256, 1, 1, 256, false>(nullptr, a, s);
+    case 2:
+      return tin ? launch_stage<2, 32, 8, 1, 288, true>(tin, a, s) : launch_stage<2, 32, 8, 1, 288, false>(nullptr, a, s);
+    case 3:
+      return tin ? launch_stage<3, 8, 8, 4, 320, true>(tin, a, s) : launch_stage<3, 8, 8, 4, 320, false>(nullptr, a, s);
   }
   rsst_set_error("ndim must be 1, 2 or 3");
   return RSST_EINVAL;
@@ -473,9 +543,18 @@ int rsst_launch_cfl_fp64(const double* U, const Geom& g, const Phys& p, double* 
                          cudaStream_t s) {
   const int gb = grid_for(g.ncells);
   switch (g.ndim) {
-    case 1: cfl_fp64_kernel<3><<<gb, 256, 0, s>>>(U, g, p, slot_ptr, flag); break;
-    case 2: cfl_fp64_kernel<4><<<gb, 256, 0, s>>>(U, g, p, slot_ptr, flag); break;
-    default: cfl_fp64_kernel<5><<<gb, 256, 0, s>>>(U, g, p, slot_ptr, flag); break;
+    case 1:
+      if (p.covol != 0.0) cfl_fp64_kernel<3, true><<<gb, 256, 0, s>>>(U, g, p, slot_ptr, flag);
+      else cfl_fp64_kernel<3, false><<<gb, 256, 0, s>>>(U, g, p, slot_ptr, flag);
+      break;
+    case 2:
+      if (p.covol != 0.0) cfl_fp64_kernel<4, true><<<gb, 256, 0, s>>>(U, g, p, slot_ptr, flag);
+      else cfl_fp64_kernel<4, false><<<gb, 256, 0, s>>>(U, g, p, slot_ptr, flag);
+      break;
+    default:
+      if (p.covol != 0.0) cfl_fp64_kernel<5, true><<<gb, 256, 0, s>>>(U, g, p, slot_ptr, flag);
+      else cfl_fp64_kernel<5, false><<<gb, 256, 0, s>>>(U, g, p, slot_ptr, flag);
+      break;
   }
   return check_launch("cfl");
 }

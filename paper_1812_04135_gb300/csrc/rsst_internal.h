@@ -122,12 +122,16 @@ struct StageArgs {
   const float* tabr; // row-major background table [tab_len][TR_W] (TMA float32 kernels), or null
   double* dU_out;   // float64 kernels: if set, the Euler tendency of each interior cell
                     // (padded layout) is written here too (adjoint recompute)
-  int64_t stall_ns; // > 0 (failure-detection tests only): each tile of the 2D TMA kernel
+  int64_t stall_ns; // > 0 (failure-detection tests only): each tile of a TMA-staged kernel
                     // also waits this long on a barrier that nothing completes
 };
 
 // Host-side launchers (defined in the .cu files).
-int rsst_launch_stage_fp64(const StageArgs<double>& a, cudaStream_t s);
+// tin: tensor map of a.in (2D/3D: the halo tile comes in by TMA), or null
+// (plain loads; always for 1D).
+int rsst_launch_stage_fp64(const CUtensorMap* tin, const StageArgs<double>& a, cudaStream_t s);
+// Box (cells along x, y, z) of the float64 stage kernel's halo tile in 2D/3D.
+void rsst_stage_fp64_box(int ndim, int* sx, int* sy, int* sz);
 int rsst_launch_pack_fp64(const double* src, double* dst, const Geom& g, const Phys& p,
                           const double* bg, int bg_len, cudaStream_t s);
 int rsst_launch_unpack_fp64(const double* src, double* dst, const Geom& g, cudaStream_t s);
@@ -179,6 +183,7 @@ struct rsst_handle {
   PhysF pf;
   int use_tma2d;        // 2D float32 runs use the TMA-staged kernel
   int use_tma3d;        // 3D float32 runs use the TMA z-march kernel
+  int use_tma_fp64;     // 2D/3D float64 runs stage their halo tiles by TMA
   CUtensorMap tmap[2];  // tensor maps of buf[0], buf[1] (TMA kernels)
   void* adj;            // adjoint checkpoints and work arrays, or null
   int slot;

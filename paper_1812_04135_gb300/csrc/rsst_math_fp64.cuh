@@ -11,44 +11,55 @@ namespace rsst {
 // Equation of state (Sec. 3.2: the reduced equations hold for a general
 // EOS; the pressure tendency needs (de/dP)_rho and (de/drho)_P, Eqs.
 // pvs_cons_dpr / pvs_cons_therm).  The float64 step reads its
-// thermodynamics only through these members.  Two gases: the ideal gas
-// (covolume b = 0, the only EOS the paper specifies), e = P/(gamma-1), and
-// the covolume (Noble-Abel) gas, P = (gamma-1) e / (1 - b rho),
-// a^2 = gamma P / (rho (1 - b rho)), (de/dP)_rho = (1 - b rho)/(gamma-1),
-// (de/drho)_P = -b P/(gamma-1).  The choice is uniform over a launch (a run's
-// b); with b = 0 every member is the ideal-gas expression unchanged.
+// thermodynamics only through these members.  Two gases, chosen at compile
+// time (CV) so that the ideal-gas kernels carry no covolume arithmetic: the
+// ideal gas (covolume b = 0, the only EOS the paper specifies),
+// e = P/(gamma-1), and the covolume (Noble-Abel) gas,
+// P = (gamma-1) e / (1 - b rho), a^2 = gamma P / (rho (1 - b rho)),
+// (de/dP)_rho = (1 - b rho)/(gamma-1), (de/drho)_P = -b P/(gamma-1).  The
+// launchers take CV = (b != 0) for a run.
 __device__ __forceinline__ double rcp_nr(double x);
 
+template <bool CV>
 struct Eos {
-  // 1 - b rho, for b != 0
+  // 1 - b rho
   __device__ static __forceinline__ double omb(const Phys& p, double rho) { return fma(-p.covol, rho, 1.0); }
   // P from the total energy E and rho |V|^2
   __device__ static __forceinline__ double pressure(const Phys& p, double rho, double E, double rhov2) {
     const double Pi = p.gm1 * E - p.hgm1 * rhov2;
-    return p.covol == 0.0 ? Pi : Pi * rcp_nr(omb(p, rho));
+    if constexpr (CV) return Pi * rcp_nr(omb(p, rho));
+    return Pi;
   }
   __device__ static __forceinline__ double sound2(const Phys& p, double rho, double P, double inv_rho) {
-    return p.covol == 0.0 ? p.gamma * P * inv_rho : p.gamma * P * inv_rho * rcp_nr(omb(p, rho));
+    if constexpr (CV) return p.gamma * P * inv_rho * rcp_nr(omb(p, rho));
+    return p.gamma * P * inv_rho;
   }
   // (a/xi)^2 for a constant xi, with gamma/xi^2 folded into one constant
   __device__ static __forceinline__ double sound2_over_xi2(const Phys& p, double rho, double P, double inv_rho) {
-    return p.covol == 0.0 ? p.gamma_xi2 * (P * inv_rho) : p.gamma_xi2 * (P * inv_rho) * rcp_nr(omb(p, rho));
+    if constexpr (CV) return p.gamma_xi2 * (P * inv_rho) * rcp_nr(omb(p, rho));
+    return p.gamma_xi2 * (P * inv_rho);
   }
   __device__ static __forceinline__ double internal_energy(const Phys& p, double rho, double P) {
-    return p.covol == 0.0 ? P * p.inv_gm1 : P * p.inv_gm1 * omb(p, rho);
+    if constexpr (CV) return P * p.inv_gm1 * omb(p, rho);
+    return P * p.inv_gm1;
   }
   __device__ static __forceinline__ double de_dP(const Phys& p, double rho, double P) {
-    return p.covol == 0.0 ? p.inv_gm1 : p.inv_gm1 * omb(p, rho);
+    if constexpr (CV) return p.inv_gm1 * omb(p, rho);
+    return p.inv_gm1;
   }
   __device__ static __forceinline__ double inv_de_dP(const Phys& p, double rho, double P) {
-    return p.covol == 0.0 ? p.gm1 : p.gm1 * rcp_nr(omb(p, rho));
+    if constexpr (CV) return p.gm1 * rcp_nr(omb(p, rho));
+    return p.gm1;
   }
-  __device__ static __forceinline__ double de_drho(const Phys& p, double rho, double P) {
-    return p.covol == 0.0 ? 0.0 : -p.covol * P * p.inv_gm1;
+  // (0.5 |V|^2 - (de/drho)_P) of the pressure tendency
+  __device__ static __forceinline__ double half_v2_minus_de_drho(const Phys& p, double v2, double P) {
+    if constexpr (CV) return fma(p.covol * p.inv_gm1, P, 0.5 * v2);
+    return 0.5 * v2;
   }
   // a state the EOS admits: 1 - b rho > 0 (always true for the ideal gas)
   __device__ static __forceinline__ bool admissible(const Phys& p, double rho) {
-    return p.covol == 0.0 || omb(p, rho) > 0.0;
+    if constexpr (CV) return omb(p, rho) > 0.0;
+    return true;
   }
 };
 
@@ -159,16 +170,17 @@ __device__ __forceinline__ double f_of(double a2, const Phys& p) {
 }
 
 // a/xi of a state for c_tot: constant xi as sqrt((a/xi)^2), or the C_max law.
+template <bool CV>
 __device__ __forceinline__ double ctot_sound(const Phys& p, double rho, double P, double ir) {
-  if (p.use_cmax) return sound_over_xi(Eos::sound2(p, rho, P, ir), p);
-  return sqrt_ctot(Eos::sound2_over_xi2(p, rho, P, ir));
+  if (p.use_cmax) return sound_over_xi(Eos<CV>::sound2(p, rho, P, ir), p);
+  return sqrt_ctot(Eos<CV>::sound2_over_xi2(p, rho, P, ir));
 }
 
 // The Euler flux along dimension D, F, and the approximate RSST
 // characteristic speed c_tot = |V| + a/xi of one state (Eq. pvs_dt0; Sec. 4.2)
 // as a float pair ch + cl: for a constant xi from ctot_pair on the float32
 // pipe, under the C_max law from the float64 form.
-template <int NV, int D>
+template <int NV, int D, bool CV = false>
 __device__ __forceinline__ void euler_flux(const double (&q)[NV], const Phys& p,
                                            double (&F)[NV], float& ch, float& cl) {
   constexpr int ND = NV - 2;
@@ -181,13 +193,13 @@ __device__ __forceinline__ void euler_flux(const double (&q)[NV], const Phys& p,
     v[e] = q[1 + e] * ir;
     v2 += v[e] * v[e];
   }
-  const double P = Eos::pressure(p, rho, q[NV - 1], rho * v2);
+  const double P = Eos<CV>::pressure(p, rho, q[NV - 1], rho * v2);
   if (p.use_cmax) {
-    const double c = sqrt_ctot(v2) + ctot_sound(p, rho, P, ir);
+    const double c = sqrt_ctot(v2) + ctot_sound<CV>(p, rho, P, ir);
     ch = __double2float_rn(c);
     cl = __double2float_rn(c - (double)ch);
   } else {
-    ctot_pair(v2, Eos::sound2_over_xi2(p, rho, P, ir), ch, cl);
+    ctot_pair(v2, Eos<CV>::sound2_over_xi2(p, rho, P, ir), ch, cl);
   }
   F[0] = q[1 + D];
 #pragma unroll
@@ -199,13 +211,13 @@ __device__ __forceinline__ void euler_flux(const double (&q)[NV], const Phys& p,
 // with alpha = max(c_tot(qL), c_tot(qR)), ties to the left state (Sec. 4.2,
 // step 4).  The factor 1/2 is exact and left to the caller (it folds into
 // the divergence's 1/dx), which saves the halvings inside the fluxes.
-template <int NV, int D>
+template <int NV, int D, bool CV = false>
 __device__ __forceinline__ void llf_flux_x2(const double (&qL)[NV], const double (&qR)[NV],
                                             const Phys& p, double (&G)[NV]) {
   double FL[NV], FR[NV];
   float hL, lL, hR, lR;
-  euler_flux<NV, D>(qL, p, FL, hL, lL);
-  euler_flux<NV, D>(qR, p, FR, hR, lR);
+  euler_flux<NV, D, CV>(qL, p, FL, hL, lL);
+  euler_flux<NV, D, CV>(qR, p, FR, hR, lR);
   const bool left = hL > hR || (hL == hR && lL >= lR);  // normalised pairs order like their values
   const double alpha = f2d_bits(left ? hL : hR) + f2d_bits(left ? lL : lR);
 #pragma unroll
@@ -243,7 +255,7 @@ __device__ __forceinline__ double mc_slope(double a, double b) {
 // with dP = (gamma-1)(V^2/2 drho - V.dm + dE) (Eq. pvs_dt_dpr, ideal gas),
 // evaluated at the cell centre of the stage state; force terms
 // (0, rho F, m.F) of App. B are added after (dP excludes them).
-template <int NV>
+template <int NV, bool CV = false>
 __device__ __forceinline__ void rsst_rhs(const double (&q)[NV], double (&dU)[NV], const Phys& p) {
   constexpr int ND = NV - 2;
   const double rho = q[0];
@@ -257,17 +269,17 @@ __device__ __forceinline__ void rsst_rhs(const double (&q)[NV], double (&dU)[NV]
       v2 += v[e] * v[e];
       vdm += v[e] * dU[1 + e];
     }
-    const double P = Eos::pressure(p, rho, q[NV - 1], rho * v2);
-    const double e_int = Eos::internal_energy(p, rho, P);
+    const double P = Eos<CV>::pressure(p, rho, q[NV - 1], rho * v2);
+    const double e_int = Eos<CV>::internal_energy(p, rho, P);
     const double kin = 0.5 * rho * v2;
     double s, r0, rv, rE;  // r = (r0, rv * V, rE); rv in {0, 1/a^2, 1}
     const int var = p.variant;
     if (var == RSST_PVS || var == RSST_PMS || var == RSST_PD) {
-      s = Eos::inv_de_dP(p, rho, P) * ((0.5 * v2 - Eos::de_drho(p, rho, P)) * dU[0] - vdm + dU[NV - 1]);
+      s = Eos<CV>::inv_de_dP(p, rho, P) * (Eos<CV>::half_v2_minus_de_drho(p, v2, P) * dU[0] - vdm + dU[NV - 1]);
       if (var == RSST_PD) {
-        r0 = 0.0; rv = 0.0; rE = Eos::de_dP(p, rho, P);
+        r0 = 0.0; rv = 0.0; rE = Eos<CV>::de_dP(p, rho, P);
       } else {
-        const double ia2 = rcp_nr(Eos::sound2(p, rho, P, ir));  // 1/a^2
+        const double ia2 = rcp_nr(Eos<CV>::sound2(p, rho, P, ir));  // 1/a^2
         r0 = ia2;
         rv = (var == RSST_PVS) ? ia2 : 0.0;
         rE = (var == RSST_PVS ? (e_int + P + kin) : (e_int + P - kin)) * ia2 * ir;
@@ -278,7 +290,7 @@ __device__ __forceinline__ void rsst_rhs(const double (&q)[NV], double (&dU)[NV]
       rv = (var == RSST_DVS) ? 1.0 : 0.0;
       rE = (var == RSST_DVS ? (e_int + P + kin) : (e_int + P - kin)) * ir;
     }
-    const double fs = f_of(Eos::sound2(p, rho, P, ir), p) * s;
+    const double fs = f_of(Eos<CV>::sound2(p, rho, P, ir), p) * s;
     dU[0] -= fs * r0;
 #pragma unroll
     for (int e = 0; e < ND; ++e) dU[1 + e] -= fs * (rv * v[e]);
@@ -296,7 +308,7 @@ __device__ __forceinline__ void rsst_rhs(const double (&q)[NV], double (&dU)[NV]
 }
 
 // CFL rate sum_d c_tot/dx_d of a cell and its physical-state check.
-template <int NV>
+template <int NV, bool CV = false>
 __device__ __forceinline__ double cfl_rate(const double (&q)[NV], const Phys& p, bool& ok) {
   constexpr int ND = NV - 2;
   const double rho = q[0];
@@ -309,9 +321,9 @@ __device__ __forceinline__ double cfl_rate(const double (&q)[NV], const Phys& p,
     v2 += ve * ve;
     fin = fin && isfinite(q[1 + e]);
   }
-  const double P = Eos::pressure(p, rho, q[NV - 1], rho * v2);
-  ok = fin && rho > 0.0 && P > 0.0 && Eos::admissible(p, rho);
-  const double c = sqrt_ctot(v2) + ctot_sound(p, rho, P, ir);
+  const double P = Eos<CV>::pressure(p, rho, q[NV - 1], rho * v2);
+  ok = fin && rho > 0.0 && P > 0.0 && Eos<CV>::admissible(p, rho);
+  const double c = sqrt_ctot(v2) + ctot_sound<CV>(p, rho, P, ir);
   return c * p.sum_inv_dx;
 }
 

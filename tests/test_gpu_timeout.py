@@ -1,12 +1,13 @@
 """Failure detection on the device without a GPU fault.
 
 Every wait of the TMA-staged kernels is bounded.  The library's test hook
-makes each tile of the 2D float32-perturbation kernel, after its own copy
-has landed, also wait on a shared-memory barrier that nothing completes, with
-a 1 ms limit.  The wait runs out, the kernel sets the run's timeout flag and
-returns; the next synchronous call must return RSST_ETIMEOUT (not
-RSST_ENONPHYSICAL), the context must stay usable, and a fresh state must then
-step to the oracle's result."""
+makes each tile of a TMA-staged kernel (2D float32 perturbation: after its
+own copy has landed; 3D float32 z-march and 2D/3D float64: with a copy still
+in flight) also wait on a shared-memory barrier that nothing completes, with
+a 1 ms limit.  The wait runs out, the kernel sets the run's timeout flag,
+waits (bounded) for any copy it issued, and returns; the next synchronous
+call must return RSST_ETIMEOUT (not RSST_ENONPHYSICAL), the context must stay
+usable, and a fresh state must then step to the oracle's result."""
 import pytest
 import torch
 
@@ -84,6 +85,33 @@ def test_3d_wait_runs_out_drains_and_is_reported():
         s.close()
 
 
+@pytest.mark.parametrize("case", ["shear2d", "polytrope3d"])
+def test_fp64_wait_runs_out_drains_and_is_reported(case):
+    """The float64 stage kernel (2D and 3D halo tiles by TMA): the test wait
+    runs out with the tile's copy in flight; the kernel waits for it, flags
+    the run and returns.  A fresh state then steps to the oracle's result."""
+    if case == "shear2d":
+        w = inputs.shear_layer_2d(72, 40, xi=30.0, variant="pvs")
+    else:
+        w = inputs.polytrope_3d(24, 16, 20, xi=50.0, amp=1e-3, contrast=20.0)
+    U = torch.from_numpy(w["U"]).cuda()
+    s = rsst.Solver(w, "fp64")
+    try:
+        s.set_state(U)
+        rsst.rsst_debug_stall_wait(s.h, LIMIT_NS)
+        s.step(1)
+        with pytest.raises(rsst.RsstError) as e:
+            s.sync()
+        assert e.value.code == rsst.RSST_ETIMEOUT, str(e.value)
+        rsst.rsst_debug_stall_wait(s.h, 0)
+        s.set_state(U)
+        s.step(2)
+        err = rel_linf(s.get_state("cpu"), _oracle(w, 2), w["gamma"])
+        assert max(err) < 1e-10, err
+    finally:
+        s.close()
+
+
 def test_stall_hook_validation():
     w = inputs.shear_layer_2d(64, 32, xi=30.0, variant="pvs")
     s = rsst.Solver(w, "fp32_pert")
@@ -94,13 +122,15 @@ def test_stall_hook_validation():
             assert e.value.code == rsst.RSST_EINVAL
     finally:
         s.close()
-    s = rsst.Solver(w, "fp64")
-    try:
-        with pytest.raises(rsst.RsstError) as e:
-            rsst.rsst_debug_stall_wait(s.h, LIMIT_NS)
-        assert e.value.code == rsst.RSST_EUNSUPPORTED
-    finally:
-        s.close()
+    # kernels without a TMA-staged tile have no test wait: double-float, 1D
+    for ws, precision in ((w, "fp64_df"), (inputs.sound_wave_1d(256, xi=10.0), "fp64")):
+        s = rsst.Solver(ws, precision)
+        try:
+            with pytest.raises(rsst.RsstError) as e:
+                rsst.rsst_debug_stall_wait(s.h, LIMIT_NS)
+            assert e.value.code == rsst.RSST_EUNSUPPORTED
+        finally:
+            s.close()
 
 
 def test_batched_wait_runs_out_and_names_a_run():
