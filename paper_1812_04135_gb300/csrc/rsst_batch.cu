@@ -1,15 +1,17 @@
 // Batched float32-perturbation RSST steps: many independent 2D runs of uneven
 // size, xi and background in one persistent kernel per RK stage.
 //
-// The tiles of all runs form one ragged list (prefix sums of each run's tile
-// count).  A grid of (SMs x resident CTAs) walks that list with a fixed
-// stride; each tile looks up its run (binary search), copies the run's
-// descriptor into shared memory and runs the same TMA-staged tile routine as
-// the single-run kernel with that run's tensor map, tables, dt and CFL slot.
+// The tiles of all runs form one ragged list, with one (run, tile within the
+// run) entry per tile.  A grid of (SMs x resident CTAs) walks that list with
+// a fixed stride; each tile reads its entry (one load), the block copies the
+// run's descriptor for the stage into shared memory (eight bytes a thread,
+// one round) and runs the same TMA-staged tile routine as the single-run
+// kernel with that run's tensor map, tables, dt and CFL slot.
 // The two stages of one step are captured once per CFL-slot parity into a
 // CUDA graph and replayed.  The tile shape is chosen by a timing autotuner
 // over six candidates (optionally cached in the file named by
 // RSST_TUNE_CACHE).
+#include <cstddef>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -24,24 +26,27 @@ namespace rsst {
 
 struct BatchRun {
   CUtensorMap tmap[2];  // maps of buf[0] and buf[1] for the chosen tile shape
-  TileRun r;            // base / out filled per stage by the kernel
+  TileRun r[2];         // the run's descriptor for stage 1 and stage 2
   float* buf[2];
   double* scal;
   int tiles_x;
   int vert;
 };
 
+static_assert(sizeof(TileRun) % 8 == 0 && offsetof(BatchRun, r) % 8 == 0, "descriptor copied in 8-byte words");
+
 template <class C, int ST>
 __global__ void __launch_bounds__(C::NT) batch_stage_kernel(const BatchRun* __restrict__ runs,
-                                                             const int* __restrict__ tile_begin, int nruns,
-                                                             int total_tiles, int slot) {
+                                                             const int2* __restrict__ tile_info, int total_tiles,
+                                                             int slot) {
   constexpr int stage = ST;
+  constexpr int NW = (int)(sizeof(TileRun) / 8);
   extern __shared__ __align__(128) unsigned char smem_raw[];
   uint64_t* bar = t2_barrier<C>(smem_raw);
   float* sdt = reinterpret_cast<float*>(bar + 1);
-  int* srun = reinterpret_cast<int*>(bar + 1) + 1;
   TileRun* sr = reinterpret_cast<TileRun*>(t2_extra<C>(smem_raw));
   static_assert(sizeof(TileRun) <= 512, "run descriptor must fit the reserved shared memory");
+  static_assert(NW <= C::NT, "the descriptor is copied in one round");
   if (threadIdx.x == 0) {
     mbar_init(bar, 1);
     fence_mbar_init();
@@ -49,31 +54,22 @@ __global__ void __launch_bounds__(C::NT) batch_stage_kernel(const BatchRun* __re
   __syncthreads();
   uint32_t phase = 0;
   for (int t = blockIdx.x; t < total_tiles; t += gridDim.x) {
+    const int2 ti = tile_info[t];  // (run, tile within the run)
+    const BatchRun& br = runs[ti.x];
+    if (threadIdx.x < NW)
+      reinterpret_cast<unsigned long long*>(sr)[threadIdx.x] =
+          reinterpret_cast<const unsigned long long*>(&br.r[stage - 1])[threadIdx.x];
     if (threadIdx.x == 0) {
-      int lo = 0, hi = nruns - 1;  // last run with tile_begin <= t
-      while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (tile_begin[mid] <= t) lo = mid; else hi = mid - 1;
-      }
-      *srun = lo;
-      const BatchRun& br = runs[lo];
-      *sr = br.r;
-      sr->base = stage == 2 ? br.buf[0] : nullptr;
-      sr->out = stage == 2 ? br.buf[0] : br.buf[1];
-      sr->stage = stage;
-      const double dtd = br.r.p.cfl / br.scal[slot];
+      const double dtd = br.r[0].p.cfl / br.scal[slot];
       *sdt = (float)dtd;
-      if (stage == 1 && t == tile_begin[lo]) {
+      if (stage == 1 && ti.y == 0) {
         br.scal[slot ^ 1] = 0.0;
         br.scal[2] = dtd;
         br.scal[3] += dtd;
       }
     }
     __syncthreads();
-    const int run = *srun;
-    const BatchRun& br = runs[run];
-    const int local = t - tile_begin[run];
-    const int tx = local % br.tiles_x, ty = local / br.tiles_x;
+    const int tx = ti.y % br.tiles_x, ty = ti.y / br.tiles_x;
     const CUtensorMap* map = &br.tmap[stage == 1 ? 0 : 1];
     float rmax = 0.0f;
     bool ok = true;
@@ -85,14 +81,7 @@ __global__ void __launch_bounds__(C::NT) batch_stage_kernel(const BatchRun* __re
       // one of its remaining tiles gets the timeout flag, so no run is left
       // partly unwritten without being reported.
       if (threadIdx.x == 0) {
-        for (int u = t + gridDim.x; u < total_tiles; u += gridDim.x) {
-          int lo = 0, hi = nruns - 1;
-          while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (tile_begin[mid] <= u) lo = mid; else hi = mid - 1;
-          }
-          atomicOr(runs[lo].r.flag, RSST_FLAG_TIMEOUT);
-        }
+        for (int u = t + gridDim.x; u < total_tiles; u += gridDim.x) atomicOr(runs[tile_info[u].x].r[0].flag, RSST_FLAG_TIMEOUT);
       }
       return;
     }
@@ -124,7 +113,7 @@ struct rsst_batch {
   cudaStream_t stream;
   std::vector<rsst_handle*> runs;
   BatchRun* d_runs;
-  int* d_tile_begin;
+  int2* d_tile_info;   // per tile of the list: (run, tile within the run)
   int choice;
   int total_tiles;
   int grid;
@@ -175,8 +164,7 @@ static int build_descriptors(rsst_batch* b, int c) {
   if (!enc) { rsst_set_error("cuTensorMapEncodeTiled unavailable from the driver"); return RSST_ECUDA; }
   const int bx = CAND_BX[c], by = CAND_BY[c];
   std::vector<BatchRun> host(b->nruns);
-  std::vector<int> begin(b->nruns + 1);
-  int total = 0;
+  std::vector<int2> info;
   for (int i = 0; i < b->nruns; ++i) {
     rsst_handle* h = b->runs[i];
     BatchRun& br = host[i];
@@ -192,22 +180,35 @@ static int build_descriptors(rsst_batch* b, int c) {
       if (r != CUDA_SUCCESS) { rsst_set_error("cuTensorMapEncodeTiled failed (%d) for run %d", (int)r, i); return RSST_ECUDA; }
       br.buf[k] = (float*)h->buf[k];
     }
-    br.r.g = h->g;
-    br.r.p = h->p;
-    br.r.pf = h->pf;
-    br.r.tabr = h->d_tabr;
-    br.r.tab_len = h->bg_len;
-    br.r.flag = h->d_flag;
-    br.r.stall_ns = h->stall_ns;
+    for (int st = 0; st < 2; ++st) {
+      TileRun& r = br.r[st];
+      r.g = h->g;
+      r.p = h->p;
+      r.pf = h->pf;
+      r.tabr = h->d_tabr;
+      r.tab_len = h->bg_len;
+      r.flag = h->d_flag;
+      r.stall_ns = h->stall_ns;
+      r.stage = st + 1;
+      r.base = st == 1 ? br.buf[0] : nullptr;  // stage 2 combines with U^n in place
+      r.out = st == 1 ? br.buf[0] : br.buf[1];
+    }
     br.scal = h->d_scal;
     br.tiles_x = (h->g.n[0] + bx - 1) / bx;
     br.vert = h->d_tab ? 1 : -1;
-    begin[i] = total;
-    total += br.tiles_x * ((h->g.n[1] + by - 1) / by);
+    const int ntiles = br.tiles_x * ((h->g.n[1] + by - 1) / by);
+    for (int k = 0; k < ntiles; ++k) info.push_back(make_int2(i, k));
   }
-  begin[b->nruns] = total;
+  const int total = (int)info.size();
+  cudaFree(b->d_tile_info);
+  b->d_tile_info = nullptr;
+  if (cudaMalloc((void**)&b->d_tile_info, sizeof(int2) * info.size()) != cudaSuccess) {
+    cudaGetLastError();
+    rsst_set_error("rsst_batch: tile list allocation failed");
+    return RSST_ENOMEM;
+  }
   if (cudaMemcpy(b->d_runs, host.data(), sizeof(BatchRun) * b->nruns, cudaMemcpyHostToDevice) != cudaSuccess ||
-      cudaMemcpy(b->d_tile_begin, begin.data(), sizeof(int) * (b->nruns + 1), cudaMemcpyHostToDevice) != cudaSuccess) {
+      cudaMemcpy(b->d_tile_info, info.data(), sizeof(int2) * info.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
     rsst_set_error("batch descriptor upload failed");
     return RSST_ECUDA;
   }
@@ -249,11 +250,11 @@ static int launch_stage(rsst_batch* b, int stage, int slot) {
   cand_kernel(b->choice, &nt, &smem);
 #define RSST_BATCH_LAUNCH(C)                                                                              \
   if (stage == 1)                                                                                         \
-    batch_stage_kernel<C, 1><<<b->grid, nt, smem, b->stream>>>(b->d_runs, b->d_tile_begin, b->nruns,      \
-                                                               b->total_tiles, slot);                     \
+    batch_stage_kernel<C, 1><<<b->grid, nt, smem, b->stream>>>(b->d_runs, b->d_tile_info, b->total_tiles, \
+                                                               slot);                                     \
   else                                                                                                    \
-    batch_stage_kernel<C, 2><<<b->grid, nt, smem, b->stream>>>(b->d_runs, b->d_tile_begin, b->nruns,      \
-                                                               b->total_tiles, slot);
+    batch_stage_kernel<C, 2><<<b->grid, nt, smem, b->stream>>>(b->d_runs, b->d_tile_info, b->total_tiles, \
+                                                               slot);
   switch (b->choice) {
     case 0: RSST_BATCH_LAUNCH(TC0) break;
     case 1: RSST_BATCH_LAUNCH(TC1) break;
@@ -302,7 +303,7 @@ extern "C" void rsst_batch_destroy(rsst_batch* b) {
   destroy_graphs(b);
   for (rsst_handle* h : b->runs) rsst_destroy(h);
   cudaFree(b->d_runs);
-  cudaFree(b->d_tile_begin);
+  cudaFree(b->d_tile_info);
   delete b;
 }
 
@@ -320,7 +321,7 @@ extern "C" int rsst_batch_init(rsst_batch** out, int32_t nruns, const rsst_confi
   b->nruns = nruns;
   b->stream = (cudaStream_t)stream;
   b->d_runs = nullptr;
-  b->d_tile_begin = nullptr;
+  b->d_tile_info = nullptr;
   b->slot = 0;
   b->launches = 0;
   b->graph_ok[0] = b->graph_ok[1] = false;
@@ -333,8 +334,7 @@ extern "C" int rsst_batch_init(rsst_batch** out, int32_t nruns, const rsst_confi
     }
     b->runs.push_back(h);
   }
-  if (cudaMalloc((void**)&b->d_runs, sizeof(BatchRun) * nruns) != cudaSuccess ||
-      cudaMalloc((void**)&b->d_tile_begin, sizeof(int) * (nruns + 1)) != cudaSuccess) {
+  if (cudaMalloc((void**)&b->d_runs, sizeof(BatchRun) * nruns) != cudaSuccess) {
     cudaGetLastError();
     rsst_set_error("rsst_batch_init: descriptor allocation failed");
     rsst_batch_destroy(b);
