@@ -73,8 +73,16 @@ __global__ void __launch_bounds__(C::NT) batch_stage_kernel(const BatchRun* __re
     const CUtensorMap* map = &br.tmap[stage == 1 ? 0 : 1];
     float rmax = 0.0f;
     bool ok = true;
-    const bool fine = br.vert == 1 ? tile2d_f<C, 1, -1, -1, ST>(map, *sr, *sdt, tx, ty, smem_raw, phase, rmax, ok)
-                                   : tile2d_f<C, -1, -1, -1, ST>(map, *sr, *sdt, tx, ty, smem_raw, phase, rmax, ok);
+    // the background case and the C_max law are fixed per tile (compile-time
+    // variants of the tile routine); the form is read from the run
+    const bool cm = sr->pf.use_cmax != 0;
+    bool fine;
+    if (br.vert == 1)
+      fine = cm ? tile2d_f<C, 1, -1, 1, ST>(map, *sr, *sdt, tx, ty, smem_raw, phase, rmax, ok)
+                : tile2d_f<C, 1, -1, 0, ST>(map, *sr, *sdt, tx, ty, smem_raw, phase, rmax, ok);
+    else
+      fine = cm ? tile2d_f<C, -1, -1, 1, ST>(map, *sr, *sdt, tx, ty, smem_raw, phase, rmax, ok)
+                : tile2d_f<C, -1, -1, 0, ST>(map, *sr, *sdt, tx, ty, smem_raw, phase, rmax, ok);
     if (!fine) {
       // A bounded wait gave up (the tile routine has already waited for its
       // copy).  This block leaves the rest of the stage: every run that owns
