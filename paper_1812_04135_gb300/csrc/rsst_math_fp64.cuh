@@ -323,8 +323,13 @@ __device__ __forceinline__ double cfl_rate(const double (&q)[NV], const Phys& p,
   }
   const double P = Eos<CV>::pressure(p, rho, q[NV - 1], rho * v2);
   ok = fin && rho > 0.0 && P > 0.0 && Eos<CV>::admissible(p, rho);
-  const double c = sqrt_ctot(v2) + ctot_sound<CV>(p, rho, P, ir);
-  return c * p.sum_inv_dx;
+  if (p.use_cmax) return (sqrt_ctot(v2) + ctot_sound<CV>(p, rho, P, ir)) * p.sum_inv_dx;
+  // c_tot as the float pair of the LLF speed (relative error below 2^-41,
+  // tighter than the float64-pipe square root's 2^-40), on the float32 and
+  // integer pipes
+  float ch, cl;
+  ctot_pair(v2, Eos<CV>::sound2_over_xi2(p, rho, P, ir), ch, cl);
+  return (f2d_bits(ch) + f2d_bits(cl)) * p.sum_inv_dx;
 }
 
 }  // namespace rsst
