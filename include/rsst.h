@@ -367,8 +367,9 @@ int64_t rsst_kernel_launches(const rsst_handle* h);
  * the direct float64 form (plus 2^20 if a c_tot square root misses one of
  * its special cases: 0 and subnormal -> 0, negative and NaN -> NaN, or the
  * float-to-double bit conversion a case); and the largest relative
- * difference between either c_tot square root (the float64 one of the CFL
- * rate and the adjoint, the float-pair one of the LLF speed) and CUDA's
+ * difference between either c_tot square root (the float64 one of the
+ * adjoint and the C_max law, the float-pair one of the LLF speed and the CFL
+ * rate) and CUDA's
  * sqrt (x in [2^-200, 2^200]).  All outputs are host pointers.
  * Synchronous, current device. */
 int rsst_math_selftest(int32_t n, double* rcp_max_ulp, int32_t* mc_mismatches, double* sqrt_max_rel);
