@@ -66,23 +66,35 @@ __device__ __forceinline__ double sound_term(double a2, const Phys& p) {
   return sqrt_ctot(a2) * p.inv_xi;
 }
 
-// Euler flux along D and c_tot = |V| + a/xi of one state (Sec. 4.2).
-template <int NV, int D>
-__device__ __forceinline__ void euler_flux_d(const double (&q)[NV], const Phys& p, double (&F)[NV], double& c) {
+// The forward values of one face state that the reverse of its flux reuses:
+// 1/rho, V, |V|^2, P, a^2, |V| and (constant xi) a.
+template <int NV>
+struct StateFwd {
+  double ir, v[NV - 2], v2, P, a2, sv, sa;
+};
+
+// c_tot = |V| + a/xi of one face state (Sec. 4.2; the LLF speed), keeping the
+// values its flux's reverse needs.  (The flux itself enters the VJP only
+// through its derivatives.)
+template <int NV>
+__device__ __forceinline__ double state_fwd(const double (&q)[NV], const Phys& p, StateFwd<NV>& w) {
   constexpr int ND = NV - 2;
   const double rho = q[0];
-  const double ir = rcp_nr(rho);
-  double v[ND];
-  double v2 = 0.0;
+  w.ir = rcp_nr(rho);
+  w.v2 = 0.0;
   for (int e = 0; e < ND; ++e) {
-    v[e] = q[1 + e] * ir;
-    v2 += v[e] * v[e];
+    w.v[e] = q[1 + e] * w.ir;
+    w.v2 += w.v[e] * w.v[e];
   }
-  const double P = p.gm1 * (q[NV - 1] - 0.5 * (rho * v2));
-  c = speed_of(v2) + sound_term(p.gamma * P * ir, p);
-  F[0] = q[1 + D];
-  for (int e = 0; e < ND; ++e) F[1 + e] = (e == D) ? q[1 + e] * v[D] + P : q[1 + e] * v[D];
-  F[NV - 1] = (q[NV - 1] + P) * v[D];
+  w.P = p.gm1 * (q[NV - 1] - 0.5 * (rho * w.v2));
+  w.a2 = p.gamma * w.P * w.ir;
+  w.sv = speed_of(w.v2);
+  if (p.use_cmax) {
+    w.sa = 0.0;
+    return w.sv + sound_term(w.a2, p);
+  }
+  w.sa = sqrt_ctot(w.a2);
+  return w.sv + w.sa * p.inv_xi;
 }
 
 // Face states of the face between u0 | u1 from the stencil (um, u0 | u1, up):
@@ -100,24 +112,19 @@ __device__ __forceinline__ void face_states(const double (&s)[4][NV], double (&q
   }
 }
 
-// Reverse of euler_flux_d at q: adds dF^T dF/dq + dc dc/dq to dq and returns
-// dF^T dF/d(1/xi) + dc dc/d(1/xi).  Hand-derived chain rule through
-// v = m/rho, P = (gamma-1)(E - rho|v|^2/2), a^2 = gamma P/rho.
+// Reverse of the Euler flux along D (F_D = (m_D, m V_D + P e_D, (E + P) V_D))
+// and of c_tot at q, with w = state_fwd's values at q: adds dF^T dF/dq +
+// dc dc/dq to dq and returns dF^T dF/d(1/xi) + dc dc/d(1/xi).  Hand-derived
+// chain rule through v = m/rho, P = (gamma-1)(E - rho|v|^2/2), a^2 = gamma P/rho.
 template <int NV, int D>
-__device__ __forceinline__ double flux_vjp(const double (&q)[NV], const Phys& p, const double (&dF)[NV], double dc,
-                                           double (&dq)[NV]) {
+__device__ __forceinline__ double flux_vjp(const double (&q)[NV], const Phys& p, const StateFwd<NV>& w,
+                                           const double (&dF)[NV], double dc, double (&dq)[NV]) {
   constexpr int ND = NV - 2;
   const double rho = q[0], E = q[NV - 1];
-  const double ir = rcp_nr(rho);
-  double v[ND], dv[ND];
-  double v2 = 0.0;
-  for (int e = 0; e < ND; ++e) {
-    v[e] = q[1 + e] * ir;
-    v2 += v[e] * v[e];
-    dv[e] = 0.0;
-  }
-  const double P = p.gm1 * (E - 0.5 * (rho * v2));
-  const double a2 = p.gamma * P * ir;
+  const double ir = w.ir, v2 = w.v2, P = w.P, a2 = w.a2;
+  const double(&v)[ND] = w.v;
+  double dv[ND];
+  for (int e = 0; e < ND; ++e) dv[e] = 0.0;
   double dP = dF[1 + D] + dF[NV - 1] * v[D], dv2 = 0.0, drho = 0.0, dE = dF[NV - 1] * v[D], dinv_xi = 0.0;
   dq[1 + D] += dF[0];
   for (int e = 0; e < ND; ++e) {
@@ -125,7 +132,7 @@ __device__ __forceinline__ double flux_vjp(const double (&q)[NV], const Phys& p,
     dv[D] += dF[1 + e] * q[1 + e];
   }
   dv[D] += dF[NV - 1] * (E + P);
-  if (v2 > 0.0) dv2 += dc * 0.5 * rcp_nr(sqrt_ctot(v2));
+  if (v2 > 0.0) dv2 += dc * 0.5 * rcp_nr(w.sv);
   double da2 = 0.0;
   if (p.use_cmax) {  // g = sqrt(u), u = a2 / t, t = sqrt(w), w = 1 + a2^2 / C^4
     const double w = 1.0 + (a2 * a2) * p.inv_cmax4, t = sqrt(w), it = rcp_nr(t), u = a2 * it;
@@ -135,7 +142,7 @@ __device__ __forceinline__ double flux_vjp(const double (&q)[NV], const Phys& p,
       da2 += du * it + dt * it * a2 * p.inv_cmax4;
     }
   } else {
-    const double s = sqrt_ctot(a2);
+    const double s = w.sa;
     dinv_xi += dc * s;
     if (a2 > 0.0) da2 += dc * p.inv_xi * 0.5 * rcp_nr(s);
   }
@@ -154,17 +161,19 @@ __device__ __forceinline__ double flux_vjp(const double (&q)[NV], const Phys& p,
   return dinv_xi;
 }
 
-// Reverse of face_flux: G[k] = phi^T dF/d(stencil cell k), and the return
+// Reverse of the face's LLF flux (Sec. 4.2, steps 2-4, through its MUSCL-MC
+// states): G[k] = phi^T dF/d(stencil cell k), and the return
 // value phi^T dF/d(1/xi).  The forward branches (MC branch, LLF side) are
 // recomputed and held.
 template <int NV, int D>
 __device__ __forceinline__ double face_vjp(const double (&s)[4][NV], const double (&phi)[NV], const Phys& p,
                                            double (&G)[4][NV]) {
-  double qL[NV], qR[NV], FL[NV], FR[NV], cL, cR;
+  double qL[NV], qR[NV];
   int bL[NV], bR[NV];
   face_states<NV>(s, qL, qR, bL, bR);
-  euler_flux_d<NV, D>(qL, p, FL, cL);
-  euler_flux_d<NV, D>(qR, p, FR, cR);
+  StateFwd<NV> wL, wR;
+  const double cL = state_fwd<NV>(qL, p, wL);
+  const double cR = state_fwd<NV>(qR, p, wR);
   const bool left = cL >= cR;
   const double alpha = left ? cL : cR;
   double dF[NV], dqL[NV], dqR[NV], dalpha = 0.0;
@@ -174,8 +183,8 @@ __device__ __forceinline__ double face_vjp(const double (&s)[4][NV], const doubl
     dqR[v] = -0.5 * alpha * phi[v];
     dalpha -= 0.5 * phi[v] * (qR[v] - qL[v]);
   }
-  double dinv_xi = flux_vjp<NV, D>(qL, p, dF, left ? dalpha : 0.0, dqL);
-  dinv_xi += flux_vjp<NV, D>(qR, p, dF, left ? 0.0 : dalpha, dqR);
+  double dinv_xi = flux_vjp<NV, D>(qL, p, wL, dF, left ? dalpha : 0.0, dqL);
+  dinv_xi += flux_vjp<NV, D>(qR, p, wR, dF, left ? 0.0 : dalpha, dqR);
   for (int v = 0; v < NV; ++v) {
     double da, db;
     // qL = u0 + MC(u0 - um, u1 - u0)/2
