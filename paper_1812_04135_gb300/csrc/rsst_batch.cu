@@ -53,14 +53,28 @@ __global__ void __launch_bounds__(C::NT) batch_stage_kernel(const BatchRun* __re
   }
   __syncthreads();
   uint32_t phase = 0;
-  for (int t = blockIdx.x; t < total_tiles; t += gridDim.x) {
-    const int2 ti = tile_info[t];  // (run, tile within the run)
-    const BatchRun& br = runs[ti.x];
-    if (threadIdx.x < NW)
-      reinterpret_cast<unsigned long long*>(sr)[threadIdx.x] =
-          reinterpret_cast<const unsigned long long*>(&br.r[stage - 1])[threadIdx.x];
+  // The next tile's list entry, this thread's word of its run descriptor and
+  // (thread 0) its CFL slot value are loaded one tile ahead, so that no
+  // dependent global load stands between two tiles.
+  int t = blockIdx.x;
+  int2 ti = make_int2(0, 0);
+  unsigned long long dword = 0ull;
+  double cfl = 0.0, cmax_slot = 1.0;
+  auto fetch = [&](int u, int2& e) {
+    e = tile_info[u];
+    const BatchRun& rb = runs[e.x];
+    if (threadIdx.x < NW) dword = reinterpret_cast<const unsigned long long*>(&rb.r[stage - 1])[threadIdx.x];
     if (threadIdx.x == 0) {
-      const double dtd = br.r[0].p.cfl / br.scal[slot];
+      cfl = rb.r[0].p.cfl;
+      cmax_slot = rb.scal[slot];
+    }
+  };
+  if (t < total_tiles) fetch(t, ti);
+  for (; t < total_tiles; t += gridDim.x) {
+    const BatchRun& br = runs[ti.x];
+    if (threadIdx.x < NW) reinterpret_cast<unsigned long long*>(sr)[threadIdx.x] = dword;
+    if (threadIdx.x == 0) {
+      const double dtd = cfl / cmax_slot;
       *sdt = (float)dtd;
       if (stage == 1 && ti.y == 0) {
         br.scal[slot ^ 1] = 0.0;
@@ -69,6 +83,8 @@ __global__ void __launch_bounds__(C::NT) batch_stage_kernel(const BatchRun* __re
       }
     }
     __syncthreads();
+    int2 tnext = ti;
+    if (t + (int)gridDim.x < total_tiles) fetch(t + gridDim.x, tnext);
     const int tx = ti.y % br.tiles_x, ty = ti.y / br.tiles_x;
     const CUtensorMap* map = &br.tmap[stage == 1 ? 0 : 1];
     float rmax = 0.0f;
@@ -98,6 +114,7 @@ __global__ void __launch_bounds__(C::NT) batch_stage_kernel(const BatchRun* __re
       block_max_to<C::NT>((double)rmax, br.scal + (slot ^ 1), t2_sred<C>(smem_raw));
     }
     __syncthreads();  // the descriptor copy is rewritten for the next tile
+    ti = tnext;
   }
 }
 
